@@ -1,0 +1,105 @@
+"""Pins of the oracle's streaming, boundaries and hydrodynamics (Eqs. 1, 12, 13,
+15; walls and open ends of Section 3.3) against conservation laws and closed-form
+single-phase flows."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_01756_gb300 import inputs
+
+
+def run(nx, ny, p, rho0, steps, T=None):
+    o = oracle.Oracle(nx, ny, p)
+    o.set_fields(rho0, T)
+    o.step(steps)
+    return o
+
+
+@pytest.mark.parametrize("y_bc", [inputs.Y_PERIODIC, inputs.Y_WALLS])
+def test_mass_is_conserved_in_a_closed_box(y_bc):
+    nx, ny = 24, 20
+    p = inputs.base_params(x_bc=inputs.X_PERIODIC, y_bc=y_bc)
+    rho0 = inputs.noisy_density(nx, ny, 0.5, 0.05, seed=3)
+    o = oracle.Oracle(nx, ny, p)
+    o.set_fields(rho0)
+    m0, _ = o.mass_heat()
+    assert m0 == pytest.approx(rho0.sum(), rel=1e-15)
+    o.step(300)
+    m1, _ = o.mass_heat()
+    assert abs(m1 - m0) <= 1e-12 * m0
+    assert o.status == 0
+
+
+def test_zou_he_imposes_inlet_velocity_and_outlet_density():
+    """Single phase (no force): at time t the inlet nodes carry u = (u_in(t), 0) and
+    the outlet nodes rho = rho_out, except the corner nodes whose wall links were
+    bounced back."""
+    nx, ny = 30, 12
+    p = inputs.base_params(multiphase=0, thermal=0, u_amp=0.01, u_period=40.0, rho_out=1.02)
+    o = run(nx, ny, p, np.ones((ny, nx)), 57)
+    rho, ux, uy, _ = o.fields()
+    u_in = 0.01 * np.sin(2 * np.pi * 57 / 40.0)
+    np.testing.assert_allclose(ux[1:-1, 0], u_in, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(uy[1:-1, 0], 0.0, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(rho[1:-1, -1], 1.02, rtol=1e-14)
+    np.testing.assert_allclose(uy[1:-1, -1], 0.0, rtol=0, atol=1e-15)
+
+
+def test_set_fields_reproduces_equilibrium_at_rest():
+    nx, ny = 10, 6
+    p = inputs.base_params(multiphase=0, thermal=0)
+    rho0 = inputs.noisy_density(nx, ny, 0.4, 0.01, seed=1)
+    o = oracle.Oracle(nx, ny, p)
+    o.set_fields(rho0)
+    f = o.populations()
+    W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    # inlet column at t = 0 has u_in = 0: equilibrium reproduced everywhere except
+    # the outlet column, where the density rule replaces f3, f6, f7
+    np.testing.assert_allclose(f[:, :, :-1], W[:, None, None] * rho0[None, :, :-1], rtol=1e-15)
+
+
+def poiseuille_profile(ny, g, nu):
+    y = np.arange(ny) + 0.5  # half-way walls at y = -1/2 and y = ny - 1/2
+    return g / (2 * nu) * y * (ny - y)
+
+
+@pytest.mark.parametrize("s_q", [1.1, 8 * (2 - 1.0) / (8 - 1.0)])
+def test_poiseuille_channel(s_q):
+    """Body-force-driven channel between half-way bounce-back walls: steady
+    u(y) = g/(2 nu) (y + 1/2)(ny - 1/2 - y), nu = (1/s_nu - 1/2)/3.  With
+    s_q = 8(2 - s_nu)/(8 - s_nu) the MRT bounce-back solution is exact."""
+    ny, g = 16, 1e-6
+    p = inputs.base_params(multiphase=0, thermal=0, x_bc=0, y_bc=1, gx=g, rho_g=0.0, s_q=s_q)
+    o = run(2, ny, p, np.ones((ny, 2)), 6000)
+    _, ux, uy, _ = o.fields()
+    ref = poiseuille_profile(ny, g, 1.0 / 6.0)
+    err = np.abs(ux[:, 0] - ref).max() / ref.max()
+    tol = 1e-9 if s_q != 1.1 else 2e-3
+    assert err < tol, err
+    assert np.abs(uy).max() < 1e-15
+
+
+def womersley(ny, g0, omega, nu, t):
+    # exact Stokes solution for u_t = nu u_yy + g0 cos(omega t), u = 0 at the walls
+    y = np.arange(ny) + 0.5 - ny / 2.0
+    k = np.sqrt(1j * omega / nu)
+    shape = 1.0 - np.cosh(k * y) / np.cosh(k * ny / 2.0)
+    return np.real(g0 / (1j * omega) * shape * np.exp(1j * omega * t))
+
+
+@pytest.mark.slow
+def test_womersley_oscillating_channel():
+    ny, g0, period = 16, 1e-6, 400.0
+    omega = 2 * np.pi / period
+    s_nu = 1.0
+    p = inputs.base_params(multiphase=0, thermal=0, x_bc=0, y_bc=1, gx=g0, g_omega=omega,
+                           rho_g=0.0, s_q=8 * (2 - s_nu) / (8 - s_nu))
+    o = run(2, ny, p, np.ones((ny, 2)), int(5 * period))
+    worst, scale = 0.0, 0.0
+    for _ in range(8):
+        o.step(int(period / 8))
+        _, ux, _, _ = o.fields()
+        ref = womersley(ny, g0, omega, 1.0 / 6.0, o.t)
+        worst = max(worst, np.abs(ux[:, 0] - ref).max())
+        scale = max(scale, np.abs(ref).max())
+    assert worst / scale < 1e-2
