@@ -1,0 +1,324 @@
+"""Benchmark of the D2Q9 pseudopotential MRT lattice update (one step = one
+lattice update of the whole channel: streaming with boundaries, density,
+pseudopotential, forces, velocity, MRT collision and the RK4 temperature update).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun every rank advances its own
+replica of the channel (weak scaling, no data-path collective); the timed region
+is bracketed by a barrier and a device synchronize and the elapsed time is the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1803_01756_gb300 import inputs  # noqa: E402
+
+# Algorithmic bytes per cell-update (FP32 storage): populations 9 x 4 read + 9 x 4
+# written, temperature 4 read + 4 written.
+BYTES_PER_CELL_UPDATE = 80
+# Per-kernel algorithmic bytes per cell for the split path (unique bytes each
+# launch must move): density/psi reads f and T and writes rho, psi; collide reads
+# f and psi and writes f and u; energy reads T, rho, u and writes T.
+SPLIT_KERNEL_BYTES = {"k_density_psi": 36 + 4 + 8, "k_collide": 36 + 4 + 36 + 8,
+                      "k_energy": 4 + 4 + 8 + 4, "k_fused_step": 80}
+L2_BYTES = 129e6
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples taken during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def setup_distributed():
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local, dist
+
+
+def time_oracle(w: dict, nx: int, ny: int, steps: int):
+    """FP64 oracle (single thread) on an nx x ny cut of workload w; returns MLUPS."""
+    import oracle
+    rho0 = inputs.noisy_density(nx, ny, inputs.RHO_V_086, w["noise"], w["seed"])
+    o = oracle.Oracle(nx, ny, w["params"])
+    o.set_fields(rho0)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return nx * ny * steps / dt / 1e6, dt
+
+
+def reference_arm(args, world, rank):
+    """The FP64 oracle as the reference arm: each step is one update of a bounded
+    cut of the channel, timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    w = inputs.workload(args.workload)
+    # size the cut so that warmup + steps take about two minutes at ~1.5 MLUPS
+    budget_cells = max(2048, int(180e6 / max(1, args.steps + args.warmup)))
+    ny = min(w["ny"], 64)
+    nx = max(32, min(w["nx"], budget_cells // ny))
+    import oracle
+    rho0 = inputs.noisy_density(nx, ny, inputs.RHO_V_086, w["noise"], w["seed"])
+    o = oracle.Oracle(nx, ny, w["params"])
+    o.set_fields(rho0)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = nx * ny * args.steps / dt / 1e6
+    sample = f"{nx}x{ny} cut of {args.workload}, {args.steps} updates per run, FP64 oracle"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "nx": nx, "ny": ny, "sample_of": [w["nx"], w["ny"]]},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+METRIC = "lattice updates per second (MLUPS), D2Q9 pseudopotential MRT + RK4 energy update"
+
+
+def our_arm(args, world, rank, local, dist):
+    import torch
+    from paper_1803_01756_gb300 import lattice as L
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    torch.cuda.set_device(local)
+    w = inputs.workload(args.workload)
+    nx, ny = w["nx"], w["ny"]
+    kernel = {"auto": L.KERNEL_AUTO, "split": L.KERNEL_SPLIT, "fused": L.KERNEL_FUSED}[args.kernel]
+
+    # CPU baseline first (rank 0, N = 1): the oracle on the host cores, before any
+    # GPU work so that nothing forks after CUDA initialisation
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        steps = args.cpu_steps
+        mlups, dt = time_oracle(w, nx, ny, steps)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{steps} updates of the full {nx}x{ny} channel ({dt:.1f} s, 1 thread)"}
+
+    stream = torch.cuda.current_stream()
+    lat = L.Lattice(nx, ny, w["params"], kernel=kernel)
+    info = lat.info()
+    rho0 = inputs.initial_density(w)
+    lat.write_fields(rho0)
+    lat.step(args.warmup, stream=stream)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K updates, device time from CUDA events on the stream ----
+    sampler = ClockSampler(local)
+    lat.timing_enable(True)
+    lat.timing_get(stream=stream)  # reset per-kernel totals
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat.step(args.steps, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    per_kernel = lat.timing_get(stream=stream)
+    lat.timing_enable(False)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    status = lat.status()
+
+    cells = nx * ny
+    value = world * cells * args.steps / (elapsed_ms / 1e3) / 1e6
+    launches = sum(n for _, n in per_kernel.values())
+
+    # dominant kernel roofline
+    peak, peak_kind = measured_peaks()
+    top = max(per_kernel.items(), key=lambda kv: kv[1][0])
+    top_name, (top_ms, top_n) = top
+    bytes_per_launch = SPLIT_KERNEL_BYTES[top_name] * cells
+    achieved = bytes_per_launch / (top_ms / top_n / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": args.traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_us": top_ms / top_n * 1e3,
+                "kernel_share": {k: v[0] / sum(x[0] for x in per_kernel.values())
+                                 for k, v in per_kernel.items()}}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        inner = args.e2e_inner
+        reps = args.e2e_reps
+        rho_h = torch.empty((ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+        rho_h[:] = rho0
+        outs = [torch.empty((ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+                for _ in range(4)]
+        dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+        lib = L.load_library()
+        sp = stream.cuda_stream
+        # one untimed job first
+        lib.lbm_write_fields(lat._h, dptr(rho_h), None, sp)
+        lib.lbm_step(lat._h, inner, sp)
+        lib.lbm_read_fields(lat._h, *[dptr(o) for o in outs], sp)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            rc = lib.lbm_write_fields(lat._h, dptr(rho_h), None, sp)
+            rc |= lib.lbm_step(lat._h, inner, sp)
+            rc |= lib.lbm_read_fields(lat._h, *[dptr(o) for o in outs], sp)
+            assert rc == 0, rc
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * cells * inner * reps / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 8 * cells / inner,
+               "d2h_bytes_per_step": 4 * 4 * info["pitch"] * ny / inner,
+               "job": f"write_fields (host rho) + {inner} updates + read_fields (host rho,u,T)"}
+    lat.close()
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "nx": nx, "ny": ny, "storage": "f32",
+                   "kernel": {1: "split", 2: "fused"}[info["kernel"]],
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"state {info['device_bytes'] / 1e6:.0f} MB > L2 129 MB; no flush",
+                   "bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
+        "hbm_frac_step": value * 1e6 / world * BYTES_PER_CELL_UPDATE / 1e9 / peak,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "status_bits": status,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="channel_4096x512", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-inner", type=int, default=100)
+    ap.add_argument("--e2e-reps", type=int, default=5)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the dominant kernel, if measured")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    world, rank, local, dist = setup_distributed()
+    try:
+        if args.impl == "reference":
+            reference_arm(args, world, rank)
+        else:
+            our_arm(args, world, rank, local, dist)
+    finally:
+        if dist:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,145 @@
+/*
+ * C ABI of the GB300 D2Q9 pseudopotential MRT lattice Boltzmann solver with the
+ * finite-difference energy equation (Zhao, Xu & Zhang, arXiv:1803.01756,
+ * Section 2, Eqs. 1-18; channel problem of Section 3.3).
+ *
+ * Conventions shared by every entry point:
+ *  - A lattice has nx * ny fluid nodes.  Host field arrays are row-major
+ *    [ny][nx] doubles (x fastest), owned by the caller.
+ *  - "stream" is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Calls enqueue their GPU work on it; calls that return host data
+ *    synchronise that stream before returning.
+ *  - Time t counts completed lattice updates.  The populations of time t carry
+ *    the inlet velocity u_amp sin(2 pi t / u_period) and step t multiplies the
+ *    body force by cos(g_omega t).
+ *  - Every call returns LBM_OK (0) or a negative LBM_ERR_* code.  A failed call
+ *    leaves the handle usable for lbm_read_* and lbm_destroy.
+ *  - Temperatures in lbm_params_t are in units of the critical temperature Tc of
+ *    Eq. 11 (Tc = 0.0778 a / (0.45724 b R)); field temperatures are absolute.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_ERR_ARG -1       /* invalid argument or size */
+#define LBM_ERR_OOM -2       /* device or host allocation failed */
+#define LBM_ERR_CUDA -3      /* a CUDA runtime call or launch failed */
+#define LBM_ERR_UNSTABLE -4  /* device status bits set (see LBM_ST_*) */
+#define LBM_ERR_TIMEOUT -5   /* a host-side wait passed its deadline */
+#define LBM_ERR_BUSY -6      /* admission refused */
+#define LBM_ERR_STATE -7     /* malformed checkpoint */
+
+/* device status bits, OR-ed by the kernels (never a trap) */
+#define LBM_ST_NAN 1u        /* NaN in a stored population or temperature */
+#define LBM_ST_PSI_NEG 2u    /* negative argument of the square root of Eq. 10 (psi set to 0) */
+#define LBM_ST_RHO_NONPOS 4u /* density <= 0 */
+#define LBM_ST_EOS_POLE 8u   /* b rho >= 1, the pole of Eq. 11 */
+#define LBM_ST_T_NONPOS 16u  /* temperature <= 0 */
+
+#define LBM_X_PERIODIC 0
+#define LBM_X_INLET_OUTLET 1 /* Zou-He velocity inlet at x=0, density outlet at x=nx-1 */
+#define LBM_Y_PERIODIC 0
+#define LBM_Y_WALLS 1        /* half-way bounce-back walls below y=0 and above y=ny-1 */
+
+#define LBM_STORAGE_F32 0    /* populations stored as FP32 f_i - w_i rho_ref */
+
+#define LBM_KERNEL_AUTO 0
+#define LBM_KERNEL_SPLIT 1   /* density/psi, collide, energy: three launches per update */
+#define LBM_KERNEL_FUSED 2   /* one launch per update */
+
+/* Problem parameters, copied by value at lbm_create (the caller keeps ownership). */
+typedef struct lbm_params {
+  double eos_a, eos_b, eos_R, eos_omega; /* Peng-Robinson EOS, Eq. 11 */
+  double G;                              /* fluid-fluid interaction strength, Eq. 9 (< 0) */
+  double Gw;                             /* fluid-wall strength, Eq. 14 */
+  double rho_w;                          /* Eq. 14 wall density; <= 0: psi_w = local psi */
+  double theta;                          /* Li forcing constant, Eq. 8 */
+  double tau_g, tau_l, rho_g, rho_l;     /* Eq. 5; rho_g is also the rho_v of Eq. 15 */
+  double s_e, s_zeta, s_q;               /* Eq. 3 rates of the e, epsilon and q moments */
+  double Cv, lambda;                     /* Eq. 16 heat capacity and conductivity */
+  double gx, gy, g_omega;                /* Eq. 15 body force (rho-rho_g) g cos(g_omega t) */
+  double T0, T_wall_left, T_wall_right, T_inlet; /* units of Tc; wall T linear in x */
+  int x_bc, y_bc;                        /* LBM_X_*, LBM_Y_* */
+  double u_amp, u_period;                /* inlet velocity; u_period = 0 gives u_amp */
+  double rho_out;                        /* outlet density */
+  int thermal;                           /* 1: advance T with Eqs. 16-18 (RK4) */
+  int multiphase;                        /* 1: pseudopotential forces, Eqs. 9, 14 */
+  int storage;                           /* LBM_STORAGE_* */
+  double rho_ref;                        /* deviation reference density; <= 0: rho_g */
+  int kernel;                            /* LBM_KERNEL_* */
+} lbm_params_t;
+
+typedef struct lbm_lattice *lbm_h;
+
+typedef struct lbm_info {
+  int nx, ny, pitch;          /* pitch: row stride of the device arrays, in elements */
+  long long t;                /* completed updates */
+  double Tc;                  /* critical temperature from Eq. 11 */
+  double T_ref, rho_ref;      /* deviation references of the stored T and populations */
+  size_t device_bytes;        /* device memory held by the handle */
+  int kernel;                 /* kernel path in use (LBM_KERNEL_SPLIT or _FUSED) */
+} lbm_info_t;
+
+/* Create a lattice of nx * ny nodes with parameters *p.  Allocates all device
+   memory of the handle on the current device; the populations start at the
+   equilibrium of rho_g at rest and T = T0.  LBM_ERR_ARG for nx, ny < 1, nx < 2
+   with open x ends, or invalid parameters; LBM_ERR_OOM if allocation fails. */
+int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out);
+
+/* Set the state at the current time from host fields: populations f = f^eq(rho, u = 0)
+   (the second-order D2Q9 equilibrium), with the open-boundary rules of the current time
+   applied to the boundary columns; T (absolute, may be NULL for uniform T0) as given.
+   rho: [ny][nx] host doubles.  Synchronises the stream. */
+int lbm_write_fields(lbm_h h, const double *rho, const double *T, void *stream);
+
+/* Advance nsteps lattice updates (Eqs. 1-18 per update): pull-streaming with bounce-back
+   and Zou-He rules, density, pseudopotential (Eqs. 10-11), forces (Eqs. 9, 14, 15),
+   velocity (Eq. 13), moment-space collision with Li forcing (Eqs. 6-8) and the RK4
+   temperature update (Eqs. 16-18).  Asynchronous: only enqueues launches on the stream. */
+int lbm_step(lbm_h h, long nsteps, void *stream);
+
+/* Copy the fields of the current time t to host arrays (any may be NULL): rho = sum f,
+   u = (sum e f + F/2) / rho (Eq. 13, force of time t), T absolute.  Synchronises the
+   stream.  Returns LBM_ERR_UNSTABLE if device status bits are set (fields still written). */
+int lbm_read_fields(lbm_h h, double *rho, double *ux, double *uy, double *T, void *stream);
+
+/* FP64 sums over all nodes of rho and rho Cv T at the current time.  Synchronises. */
+int lbm_reduce(lbm_h h, double *mass, double *heat, void *stream);
+
+/* Device status bits (LBM_ST_*) accumulated since creation; clears them when clear != 0.
+   Synchronises the stream. */
+int lbm_status(lbm_h h, unsigned *bits, int clear, void *stream);
+
+/* Checkpoint: the populations, temperature and time as an opaque byte string. */
+int lbm_state_bytes(lbm_h h, size_t *bytes);
+int lbm_read_state(lbm_h h, void *buf, size_t bytes, void *stream);
+int lbm_write_state(lbm_h h, const void *buf, size_t bytes, void *stream);
+
+int lbm_info(lbm_h h, lbm_info_t *info);
+
+/* Per-kernel CUDA-event timing of lbm_step launches.  enable != 0 starts recording
+   (events are placed around every launch, which serialises nothing but costs host time).
+   lbm_timing_get writes up to n (name, total ms, launches) triples for kernels launched
+   since the last reset and synchronises the stream. */
+int lbm_timing_enable(lbm_h h, int enable);
+int lbm_timing_get(lbm_h h, const char **names, double *total_ms, long *launches, int n,
+                   int *count, void *stream);
+
+/* Free everything the handle owns.  NULL is ignored. */
+void lbm_destroy(lbm_h h);
+
+const char *lbm_strerror(int code);
+
+/* Critical temperature of Eq. 11 for the given parameters. */
+double lbm_critical_temperature(const lbm_params_t *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

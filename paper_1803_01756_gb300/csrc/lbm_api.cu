@@ -1,0 +1,553 @@
+// Host runtime and C ABI (include/lbm.h).
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using lbm::DevParams;
+using lbm::StepScalars;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr uint32_t kStateMagic = 0x534d424cu;  // "LBMS"
+constexpr uint32_t kStateVersion = 1;
+
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t nx, ny, pitch, storage;
+  int64_t t;
+  int64_t reserved[4];
+};
+
+enum { KN_DENSITY = 0, KN_COLLIDE, KN_ENERGY, KN_FUSED, KN_COUNT };
+const char *kKernelNames[KN_COUNT] = {"k_density_psi", "k_collide", "k_energy", "k_fused_step"};
+
+struct TimedLaunch {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct lbm_lattice {
+  int device = 0;
+  int nx = 0, ny = 0, pitch = 0;
+  long long plane = 0;
+  lbm_params_t p{};
+  DevParams dp{};
+  double Tc = 0, T_ref = 0, rho_ref = 0;
+  long long t = 0;
+  int kernel = LBM_KERNEL_SPLIT;
+  int cur = 0;   // g[cur]: post-collision populations of the previous update
+  int tcur = 0;  // T[tcur]: temperature deviation of time t
+  float *g[2] = {nullptr, nullptr};
+  float *T[2] = {nullptr, nullptr};
+  float *rho = nullptr, *psi = nullptr, *ux = nullptr, *uy = nullptr;
+  unsigned *status = nullptr;
+  double *partials = nullptr, *sums = nullptr;
+  int nblocks = 1;
+  double *rho0 = nullptr;  // device staging for lbm_write_fields
+  float *host_stage = nullptr;  // pinned, plane floats
+  double *host_sums = nullptr;  // pinned, 2 doubles
+  size_t device_bytes = 0;
+  // timing
+  bool timing = false;
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> pool;
+  double total_ms[KN_COUNT] = {0, 0, 0, 0};
+  long launches[KN_COUNT] = {0, 0, 0, 0};
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaSuccess) return LBM_OK;
+  if (e == cudaErrorMemoryAllocation) return LBM_ERR_OOM;
+  return LBM_ERR_CUDA;
+}
+
+#define LBM_CUDA(expr)                          \
+  do {                                          \
+    cudaError_t _e = (expr);                    \
+    if (_e != cudaSuccess) return cuda_fail(_e); \
+  } while (0)
+
+double critical_temperature(const lbm_params_t &p) {
+  return 0.0778 * p.eos_a / (0.45724 * p.eos_b * p.eos_R);
+}
+
+bool valid_rate(double s) { return s > 0.0 && s < 2.0; }
+
+int validate(int nx, int ny, const lbm_params_t &p) {
+  if (nx < 1 || ny < 1) return LBM_ERR_ARG;
+  if (nx > (1 << 20) || ny > (1 << 20)) return LBM_ERR_ARG;
+  if (p.x_bc != LBM_X_PERIODIC && p.x_bc != LBM_X_INLET_OUTLET) return LBM_ERR_ARG;
+  if (p.y_bc != LBM_Y_PERIODIC && p.y_bc != LBM_Y_WALLS) return LBM_ERR_ARG;
+  if (p.x_bc == LBM_X_INLET_OUTLET && (nx < 2 || !(p.rho_out > 0.0))) return LBM_ERR_ARG;
+  if (!(p.eos_a > 0.0) || !(p.eos_b > 0.0) || !(p.eos_R > 0.0)) return LBM_ERR_ARG;
+  if (p.multiphase && !(p.G != 0.0)) return LBM_ERR_ARG;
+  if (p.thermal && !(p.Cv > 0.0)) return LBM_ERR_ARG;
+  if (!(p.T0 > 0.0)) return LBM_ERR_ARG;
+  if (!(p.tau_g > 0.5) || !(p.tau_l > 0.5)) return LBM_ERR_ARG;
+  if (!valid_rate(p.s_e) || !valid_rate(p.s_zeta) || !valid_rate(p.s_q)) return LBM_ERR_ARG;
+  if (p.storage != LBM_STORAGE_F32) return LBM_ERR_ARG;
+  if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_FUSED) return LBM_ERR_ARG;
+  if (p.u_period < 0.0 || std::fabs(p.u_amp) >= 1.0) return LBM_ERR_ARG;
+  return LBM_OK;
+}
+
+DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, double &T_ref,
+                 double &rho_ref) {
+  DevParams d{};
+  d.nx = nx;
+  d.ny = ny;
+  d.pitch = pitch;
+  d.plane = (long long)ny * pitch;
+  d.x_open = p.x_bc == LBM_X_INLET_OUTLET;
+  d.y_walls = p.y_bc == LBM_Y_WALLS;
+  d.multiphase = p.multiphase != 0;
+  d.thermal = p.thermal != 0;
+  Tc = critical_temperature(p);
+  T_ref = p.T0 * Tc;
+  rho_ref = p.rho_ref > 0.0 ? p.rho_ref : p.rho_g;
+  d.rho_ref = (float)rho_ref;
+  d.T_ref = (float)T_ref;
+  d.Tc = (float)Tc;
+  d.inv_Tc = (float)(1.0 / Tc);
+  d.eos_a = (float)p.eos_a;
+  d.eos_b = (float)p.eos_b;
+  d.eos_R = (float)p.eos_R;
+  d.kappa = (float)(0.37464 + 1.54226 * p.eos_omega - 0.26992 * p.eos_omega * p.eos_omega);
+  d.G = (float)p.G;
+  d.Gw = (float)p.Gw;
+  d.rho_w = (float)p.rho_w;
+  d.c_theta_e = (float)(12.0 * p.theta * p.s_e * p.G * p.G);
+  d.c_theta_z = (float)(12.0 * p.theta * p.s_zeta * p.G * p.G);
+  d.s_e = (float)p.s_e;
+  d.s_z = (float)p.s_zeta;
+  d.s_q = (float)p.s_q;
+  d.tau_g = (float)p.tau_g;
+  d.dtau = (float)(p.tau_l - p.tau_g);
+  d.rho_g = (float)p.rho_g;
+  d.inv_drho = p.rho_l != p.rho_g ? (float)(1.0 / (p.rho_l - p.rho_g)) : 0.0f;
+  d.tau_const = p.tau_g == p.tau_l || p.rho_l == p.rho_g;
+  d.s_nu_const = (float)(1.0 / p.tau_g);
+  d.gx = (float)p.gx;
+  d.gy = (float)p.gy;
+  d.Cv = (float)p.Cv;
+  d.lambda = (float)p.lambda;
+  d.tw0 = (float)(Tc * p.T_wall_left - T_ref);
+  d.tw_slope = nx > 1 ? (float)(Tc * (p.T_wall_right - p.T_wall_left) / (nx - 1)) : 0.0f;
+  d.T_inlet_dev = (float)(Tc * p.T_inlet - T_ref);
+  d.rho_out = (float)p.rho_out;
+  return d;
+}
+
+StepScalars scalars_at(const lbm_lattice *h, long long t) {
+  StepScalars s;
+  double u = h->p.u_period == 0.0 ? h->p.u_amp
+                                   : h->p.u_amp * std::sin(2.0 * kPi * (double)t / h->p.u_period);
+  s.u_in = (float)u;
+  s.gcos = (float)std::cos(h->p.g_omega * (double)t);
+  return s;
+}
+
+cudaEvent_t take_event(lbm_lattice *h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+int drain_timing(lbm_lattice *h) {
+  for (auto &tl : h->pending) {
+    LBM_CUDA(cudaEventSynchronize(tl.b));
+    float ms = 0.0f;
+    LBM_CUDA(cudaEventElapsedTime(&ms, tl.a, tl.b));
+    h->total_ms[tl.kind] += ms;
+    h->launches[tl.kind] += 1;
+    h->pool.push_back(tl.a);
+    h->pool.push_back(tl.b);
+  }
+  h->pending.clear();
+  return LBM_OK;
+}
+
+// launch wrapper that brackets the launch with events when timing is on
+template <typename F>
+int timed(lbm_lattice *h, int kind, cudaStream_t s, F &&launch) {
+  if (!h->timing) return cuda_fail(launch());
+  TimedLaunch tl{kind, take_event(h), take_event(h)};
+  if (!tl.a || !tl.b) return LBM_ERR_CUDA;
+  LBM_CUDA(cudaEventRecord(tl.a, s));
+  cudaError_t e = launch();
+  LBM_CUDA(cudaEventRecord(tl.b, s));
+  h->pending.push_back(tl);
+  if (h->pending.size() >= 32768) {
+    int rc = drain_timing(h);
+    if (rc) return rc;
+  }
+  return cuda_fail(e);
+}
+
+int compute_rho_psi(lbm_lattice *h, cudaStream_t s) {
+  StepScalars sc = scalars_at(h, h->t);
+  return cuda_fail(lbm::launch_density_psi(h->dp, h->g[h->cur], h->T[h->tcur], h->rho, h->psi,
+                                           h->status, sc, s));
+}
+
+int one_update(lbm_lattice *h, cudaStream_t s) {
+  StepScalars sc = scalars_at(h, h->t);
+  const DevParams &d = h->dp;
+  int rc;
+  if (h->kernel == LBM_KERNEL_FUSED) {
+    rc = timed(h, KN_FUSED, s, [&] {
+      return lbm::launch_fused(d, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur],
+                               h->T[1 - h->tcur], h->status, sc, s);
+    });
+    if (rc) return rc;
+  } else {
+    rc = timed(h, KN_DENSITY, s, [&] {
+      return lbm::launch_density_psi(d, h->g[h->cur], h->T[h->tcur], h->rho, h->psi, h->status,
+                                     sc, s);
+    });
+    if (rc) return rc;
+    rc = timed(h, KN_COLLIDE, s, [&] {
+      return lbm::launch_collide(d, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur], h->psi, h->ux,
+                                 h->uy, h->status, sc, true, s);
+    });
+    if (rc) return rc;
+    if (d.thermal) {
+      rc = timed(h, KN_ENERGY, s, [&] {
+        return lbm::launch_energy(d, h->T[h->tcur], h->T[1 - h->tcur], h->rho, h->ux, h->uy,
+                                  h->status, sc, s);
+      });
+      if (rc) return rc;
+    }
+  }
+  h->cur ^= 1;
+  if (d.thermal) h->tcur ^= 1;
+  h->t += 1;
+  return LBM_OK;
+}
+
+void free_all(lbm_lattice *h) {
+  cudaFree(h->g[0]);
+  cudaFree(h->g[1]);
+  cudaFree(h->T[0]);
+  cudaFree(h->T[1]);
+  cudaFree(h->rho);
+  cudaFree(h->psi);
+  cudaFree(h->ux);
+  cudaFree(h->uy);
+  cudaFree(h->status);
+  cudaFree(h->partials);
+  cudaFree(h->sums);
+  cudaFree(h->rho0);
+  if (h->host_stage) cudaFreeHost(h->host_stage);
+  if (h->host_sums) cudaFreeHost(h->host_sums);
+  for (auto &tl : h->pending) {
+    cudaEventDestroy(tl.a);
+    cudaEventDestroy(tl.b);
+  }
+  for (auto e : h->pool) cudaEventDestroy(e);
+}
+
+template <typename T>
+cudaError_t dalloc(lbm_lattice *h, T **ptr, size_t count) {
+  size_t bytes = count * sizeof(T);
+  cudaError_t e = cudaMalloc((void **)ptr, bytes);
+  if (e == cudaSuccess) h->device_bytes += bytes;
+  return e;
+}
+
+int upload_fields(lbm_lattice *h, const double *rho, const double *T, cudaStream_t s) {
+  const size_t n = (size_t)h->nx * h->ny;
+  LBM_CUDA(cudaMemcpyAsync(h->rho0, rho, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  LBM_CUDA(lbm::launch_init(h->dp, h->rho0, h->g[h->cur], s));
+  // temperature deviations through the pinned staging buffer
+  float *st = h->host_stage;
+  LBM_CUDA(cudaStreamSynchronize(s));
+  for (int y = 0; y < h->ny; y++)
+    for (int x = 0; x < h->pitch; x++) {
+      double v = 0.0;
+      if (T && x < h->nx) v = T[(size_t)y * h->nx + x] - h->T_ref;
+      st[(size_t)y * h->pitch + x] = (float)v;
+    }
+  LBM_CUDA(cudaMemcpyAsync(h->T[h->tcur], st, sizeof(float) * h->plane, cudaMemcpyHostToDevice, s));
+  LBM_CUDA(cudaStreamSynchronize(s));
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+double lbm_critical_temperature(const lbm_params_t *p) {
+  return p ? critical_temperature(*p) : 0.0;
+}
+
+const char *lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_OOM: return "out of memory";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_UNSTABLE: return "device status bits set (unstable or invalid state)";
+    case LBM_ERR_TIMEOUT: return "timeout";
+    case LBM_ERR_BUSY: return "admission refused";
+    case LBM_ERR_STATE: return "malformed checkpoint";
+    default: return "unknown error";
+  }
+}
+
+int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
+  if (!p || !out) return LBM_ERR_ARG;
+  *out = nullptr;
+  int rc = validate(nx, ny, *p);
+  if (rc) return rc;
+  lbm_lattice *h = new (std::nothrow) lbm_lattice();
+  if (!h) return LBM_ERR_OOM;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return LBM_ERR_CUDA;
+  }
+  h->nx = nx;
+  h->ny = ny;
+  h->pitch = (nx + 31) / 32 * 32;
+  h->plane = (long long)ny * h->pitch;
+  h->p = *p;
+  h->dp = derive(nx, ny, h->pitch, *p, h->Tc, h->T_ref, h->rho_ref);
+  h->kernel = LBM_KERNEL_SPLIT;
+  if (p->kernel == LBM_KERNEL_FUSED || p->kernel == LBM_KERNEL_AUTO) {
+    if (lbm::fused_supported(h->dp)) h->kernel = LBM_KERNEL_FUSED;
+    else if (p->kernel == LBM_KERNEL_FUSED) {
+      delete h;
+      return LBM_ERR_ARG;
+    }
+  }
+  h->nblocks = lbm::mass_heat_blocks(h->dp);
+  const size_t plane = (size_t)h->plane;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) e = dalloc(h, &h->g[k], 9 * plane);
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) e = dalloc(h, &h->T[k], plane);
+  if (e == cudaSuccess) e = dalloc(h, &h->rho, plane);
+  if (e == cudaSuccess) e = dalloc(h, &h->psi, plane);
+  if (e == cudaSuccess) e = dalloc(h, &h->ux, plane);
+  if (e == cudaSuccess) e = dalloc(h, &h->uy, plane);
+  if (e == cudaSuccess) e = dalloc(h, &h->status, 1);
+  if (e == cudaSuccess) e = dalloc(h, &h->partials, 2 * (size_t)h->nblocks);
+  if (e == cudaSuccess) e = dalloc(h, &h->sums, 2);
+  if (e == cudaSuccess) e = dalloc(h, &h->rho0, (size_t)nx * ny);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_stage, sizeof(float) * plane);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_sums, 2 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(unsigned));
+  // padding columns stay zero forever
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMemset(h->g[k], 0, 9 * plane * sizeof(float));
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMemset(h->T[k], 0, plane * sizeof(float));
+  if (e != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return cuda_fail(e);
+  }
+  // rest equilibrium of rho_g, T = T0
+  std::vector<double> r0((size_t)nx * ny, p->rho_g > 0.0 ? p->rho_g : h->rho_ref);
+  rc = upload_fields(h, r0.data(), nullptr, 0);
+  if (rc) {
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_h h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+}
+
+int lbm_write_fields(lbm_h h, const double *rho, const double *T, void *stream) {
+  if (!h || !rho) return LBM_ERR_ARG;
+  LBM_CUDA(cudaSetDevice(h->device));
+  return upload_fields(h, rho, T, (cudaStream_t)stream);
+}
+
+int lbm_step(lbm_h h, long nsteps, void *stream) {
+  if (!h || nsteps < 0) return LBM_ERR_ARG;
+  LBM_CUDA(cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  for (long k = 0; k < nsteps; k++) {
+    int rc = one_update(h, s);
+    if (rc) return rc;
+  }
+  return LBM_OK;
+}
+
+int lbm_status(lbm_h h, unsigned *bits, int clear, void *stream) {
+  if (!h || !bits) return LBM_ERR_ARG;
+  LBM_CUDA(cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned *hs = (unsigned *)h->host_sums;
+  LBM_CUDA(cudaMemcpyAsync(hs, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  LBM_CUDA(cudaStreamSynchronize(s));
+  *bits = *hs;
+  if (clear) {
+    LBM_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), s));
+    LBM_CUDA(cudaStreamSynchronize(s));
+  }
+  return LBM_OK;
+}
+
+int lbm_read_fields(lbm_h h, double *rho, double *ux, double *uy, double *T, void *stream) {
+  if (!h) return LBM_ERR_ARG;
+  LBM_CUDA(cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = compute_rho_psi(h, s);
+  if (rc) return rc;
+  StepScalars sc = scalars_at(h, h->t);
+  LBM_CUDA(lbm::launch_collide(h->dp, h->g[h->cur], nullptr, h->T[h->tcur], h->psi, h->ux, h->uy,
+                               h->status, sc, false, s));
+  struct Out {
+    double *dst;
+    const float *src;
+    double add;
+  } outs[4] = {{rho, h->rho, 0.0}, {ux, h->ux, 0.0}, {uy, h->uy, 0.0}, {T, h->T[h->tcur], h->T_ref}};
+  for (auto &o : outs) {
+    if (!o.dst) continue;
+    LBM_CUDA(cudaMemcpyAsync(h->host_stage, o.src, sizeof(float) * h->plane,
+                             cudaMemcpyDeviceToHost, s));
+    LBM_CUDA(cudaStreamSynchronize(s));
+    for (int y = 0; y < h->ny; y++)
+      for (int x = 0; x < h->nx; x++)
+        o.dst[(size_t)y * h->nx + x] = (double)h->host_stage[(size_t)y * h->pitch + x] + o.add;
+  }
+  unsigned bits = 0;
+  rc = lbm_status(h, &bits, 0, stream);
+  if (rc) return rc;
+  return bits ? LBM_ERR_UNSTABLE : LBM_OK;
+}
+
+int lbm_reduce(lbm_h h, double *mass, double *heat, void *stream) {
+  if (!h) return LBM_ERR_ARG;
+  LBM_CUDA(cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = compute_rho_psi(h, s);
+  if (rc) return rc;
+  LBM_CUDA(lbm::launch_mass_heat(h->dp, h->rho, h->T[h->tcur], h->T_ref, h->p.Cv, h->partials,
+                                 h->nblocks, h->sums, s));
+  LBM_CUDA(cudaMemcpyAsync(h->host_sums, h->sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  LBM_CUDA(cudaStreamSynchronize(s));
+  if (mass) *mass = h->host_sums[0];
+  if (heat) *heat = h->host_sums[1];
+  return LBM_OK;
+}
+
+int lbm_state_bytes(lbm_h h, size_t *bytes) {
+  if (!h || !bytes) return LBM_ERR_ARG;
+  *bytes = sizeof(StateHeader) + sizeof(float) * (size_t)h->plane * 10;
+  return LBM_OK;
+}
+
+int lbm_read_state(lbm_h h, void *buf, size_t bytes, void *stream) {
+  size_t need = 0;
+  if (!h || !buf || lbm_state_bytes(h, &need) || bytes < need) return LBM_ERR_ARG;
+  LBM_CUDA(cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  StateHeader hd{};
+  hd.magic = kStateMagic;
+  hd.version = kStateVersion;
+  hd.nx = h->nx;
+  hd.ny = h->ny;
+  hd.pitch = h->pitch;
+  hd.storage = h->p.storage;
+  hd.t = h->t;
+  std::memcpy(buf, &hd, sizeof(hd));
+  char *dst = (char *)buf + sizeof(hd);
+  LBM_CUDA(cudaMemcpyAsync(dst, h->g[h->cur], sizeof(float) * 9 * h->plane, cudaMemcpyDeviceToHost, s));
+  LBM_CUDA(cudaMemcpyAsync(dst + sizeof(float) * 9 * h->plane, h->T[h->tcur],
+                           sizeof(float) * h->plane, cudaMemcpyDeviceToHost, s));
+  LBM_CUDA(cudaStreamSynchronize(s));
+  return LBM_OK;
+}
+
+int lbm_write_state(lbm_h h, const void *buf, size_t bytes, void *stream) {
+  size_t need = 0;
+  if (!h || !buf || lbm_state_bytes(h, &need)) return LBM_ERR_ARG;
+  if (bytes < need) return LBM_ERR_STATE;
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.version != kStateVersion || hd.nx != h->nx || hd.ny != h->ny ||
+      hd.pitch != h->pitch || hd.storage != h->p.storage || hd.t < 0)
+    return LBM_ERR_STATE;
+  LBM_CUDA(cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const char *src = (const char *)buf + sizeof(hd);
+  LBM_CUDA(cudaMemcpyAsync(h->g[h->cur], src, sizeof(float) * 9 * h->plane, cudaMemcpyHostToDevice, s));
+  LBM_CUDA(cudaMemcpyAsync(h->T[h->tcur], src + sizeof(float) * 9 * h->plane,
+                           sizeof(float) * h->plane, cudaMemcpyHostToDevice, s));
+  LBM_CUDA(cudaStreamSynchronize(s));
+  h->t = hd.t;
+  return LBM_OK;
+}
+
+int lbm_info(lbm_h h, lbm_info_t *info) {
+  if (!h || !info) return LBM_ERR_ARG;
+  info->nx = h->nx;
+  info->ny = h->ny;
+  info->pitch = h->pitch;
+  info->t = h->t;
+  info->Tc = h->Tc;
+  info->T_ref = h->T_ref;
+  info->rho_ref = h->rho_ref;
+  info->device_bytes = h->device_bytes;
+  info->kernel = h->kernel;
+  return LBM_OK;
+}
+
+int lbm_timing_enable(lbm_h h, int enable) {
+  if (!h) return LBM_ERR_ARG;
+  h->timing = enable != 0;
+  return LBM_OK;
+}
+
+int lbm_timing_get(lbm_h h, const char **names, double *total_ms, long *launches, int n,
+                   int *count, void *stream) {
+  if (!h || n < 0) return LBM_ERR_ARG;
+  LBM_CUDA(cudaSetDevice(h->device));
+  LBM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  int rc = drain_timing(h);
+  if (rc) return rc;
+  int k = 0;
+  for (int i = 0; i < KN_COUNT; i++) {
+    if (h->launches[i] == 0) continue;
+    if (k < n) {
+      if (names) names[k] = kKernelNames[i];
+      if (total_ms) total_ms[k] = h->total_ms[i];
+      if (launches) launches[k] = h->launches[i];
+    }
+    k++;
+  }
+  if (count) *count = k;
+  for (int i = 0; i < KN_COUNT; i++) {
+    h->total_ms[i] = 0;
+    h->launches[i] = 0;
+  }
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,284 @@
+// Device-side physics of the D2Q9 pseudopotential MRT lattice update
+// (arXiv:1803.01756, Section 2).  FP32 arithmetic; populations are carried as
+// deviations g_i = f_i - w_i rho_ref and temperatures as T - T_ref, so that the
+// stored numbers are small and FP32 rounding stays far below the field values.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+// D2Q9 velocity set of Eq. 2
+__host__ __device__ constexpr int ex(int i) {
+  return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+  return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+  return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 5 + 2) & 3) + 5);
+}
+// D2Q9 lattice weights
+__host__ __device__ constexpr float wlat(int i) {
+  return i == 0 ? 4.0f / 9.0f : (i <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+// Eq. 9 interaction weights w(1) = 1/3, w(2) = 1/12
+__host__ __device__ constexpr float wpsi(int i) {
+  return i == 0 ? 0.0f : (i <= 4 ? 1.0f / 3.0f : 1.0f / 12.0f);
+}
+
+enum : unsigned {
+  ST_NAN = 1u, ST_PSI_NEG = 2u, ST_RHO_NONPOS = 4u, ST_EOS_POLE = 8u, ST_T_NONPOS = 16u
+};
+
+// Parameters as the kernels see them (derived on the host from lbm_params_t).
+struct DevParams {
+  int nx, ny, pitch;
+  int x_open, y_walls, multiphase, thermal;
+  long long plane;        // ny * pitch, elements per population plane
+  float rho_ref, T_ref;   // deviation references
+  float Tc, inv_Tc;
+  float eos_a, eos_b, eos_R, kappa;
+  float G, Gw, rho_w;     // rho_w <= 0: psi_w = local psi
+  float c_theta_e;        // 12 theta s_e G^2   ((1 - s_e/2) 12 theta / (tau_e - 1/2) = 12 theta s_e)
+  float c_theta_z;        // 12 theta s_zeta G^2
+  float s_e, s_z, s_q;
+  float tau_g, dtau, rho_g, inv_drho;  // Eq. 5: tau_g + clamp((rho - rho_g) inv_drho) dtau
+  int tau_const;          // tau_g == tau_l
+  float s_nu_const;
+  float gx, gy;
+  float Cv, lambda;
+  float tw0, tw_slope;    // wall temperature deviation at x: tw0 + tw_slope * x
+  float T_inlet_dev;
+  float rho_out;
+};
+
+// Per-update scalars computed on the host in double precision.
+struct StepScalars {
+  float u_in;   // inlet velocity of time t
+  float gcos;   // cos(g_omega t)
+};
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+  v = v < 0 ? v + n : v;
+  return v >= n ? v - n : v;
+}
+
+__device__ __forceinline__ void set_status(unsigned *status, unsigned bits) {
+  if (bits) atomicOr(status, bits);
+}
+
+// ---------------------------------------------------------------------------
+// Peng-Robinson EOS (Eq. 11) and pseudopotential (Eq. 10)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float eos_pressure(const DevParams &p, float rho, float Tabs) {
+  float r = 1.0f + p.kappa * (1.0f - sqrtf(Tabs * p.inv_Tc));
+  float phi = r * r;
+  float br = p.eos_b * rho;
+  return rho * p.eos_R * Tabs / (1.0f - br) - p.eos_a * phi * rho * rho / (1.0f + 2.0f * br - br * br);
+}
+
+// psi = sqrt(2 (P - rho/3) / G); negative argument -> 0 and a status bit
+__device__ __forceinline__ float pseudopotential(const DevParams &p, float rho, float Tabs,
+                                                 unsigned &st) {
+  float arg = 2.0f * (eos_pressure(p, rho, Tabs) - rho * (1.0f / 3.0f)) / p.G;
+  if (!(arg >= 0.0f)) {
+    st |= ST_PSI_NEG;
+    return 0.0f;
+  }
+  return sqrtf(arg);
+}
+
+// ---------------------------------------------------------------------------
+// Geometry: classification of the site (x + dx, y + dy) seen from a fluid node
+// ---------------------------------------------------------------------------
+enum : int { NB_FLUID = 0, NB_SOLID = 1, NB_INLET = 2, NB_OUTLET = 3 };
+
+// Returns the kind; for FLUID/INLET/OUTLET (xo, yo) is the fluid node supplying
+// a copied value (wrapped, or clamped at the open ends).
+__device__ __forceinline__ int classify(const DevParams &p, int x, int y, int dx, int dy,
+                                        int &xo, int &yo) {
+  int xs = x + dx, ys = y + dy;
+  if (p.y_walls) {
+    if (ys < 0 || ys >= p.ny) {
+      xo = min(max(xs, 0), p.nx - 1);
+      yo = ys < 0 ? 0 : p.ny - 1;
+      return NB_SOLID;
+    }
+  } else {
+    ys = wrapi(ys, p.ny);
+  }
+  yo = ys;
+  if (!p.x_open) {
+    xo = wrapi(xs, p.nx);
+    return NB_FLUID;
+  }
+  if (xs < 0) { xo = 0; return NB_INLET; }
+  if (xs >= p.nx) { xo = p.nx - 1; return NB_OUTLET; }
+  xo = xs;
+  return NB_FLUID;
+}
+
+// ---------------------------------------------------------------------------
+// Pull-streaming (Eq. 12 indexed by destination) with half-way bounce-back on
+// wall rows and Zou-He on the open columns (force-free form).
+// gs: post-collision deviations of the previous update.  g: pulled deviations.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pull(const DevParams &p, const float *__restrict__ gs, int x,
+                                     int y, float u_in, float g[9]) {
+  const long long c = (long long)y * p.pitch + x;
+  const bool interior = x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1;
+  if (interior) {
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+      g[i] = __ldg(gs + i * p.plane + c - ey(i) * p.pitch - ex(i));
+    return;
+  }
+  bool unknown[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    int xo, yo;
+    int k = classify(p, x, y, -ex(i), -ey(i), xo, yo);
+    unknown[i] = false;
+    if (i == 0) {
+      g[0] = __ldg(gs + c);
+    } else if (k == NB_FLUID) {
+      g[i] = __ldg(gs + i * p.plane + (long long)yo * p.pitch + xo);
+    } else {
+      g[i] = __ldg(gs + opp(i) * p.plane + c);
+      unknown[i] = (k == NB_INLET || k == NB_OUTLET);
+    }
+  }
+  if (!p.x_open) return;
+  if (x == 0) {
+    // velocity inlet: f0+f2+f4+2(f3+f6+f7) has weight sum 1 -> rho_ref + deviations
+    float U = u_in;
+    float rb = (g[0] + g[2] + g[4] + 2.0f * (g[3] + g[6] + g[7]) + p.rho_ref) / (1.0f - U);
+    if (unknown[1]) g[1] = g[3] + (2.0f / 3.0f) * rb * U;
+    if (unknown[5]) g[5] = g[7] - 0.5f * (g[2] - g[4]) + rb * U * (1.0f / 6.0f);
+    if (unknown[8]) g[8] = g[6] + 0.5f * (g[2] - g[4]) + rb * U * (1.0f / 6.0f);
+  }
+  if (x == p.nx - 1) {
+    float ro = p.rho_out;
+    float U = (g[0] + g[2] + g[4] + 2.0f * (g[1] + g[5] + g[8]) + (p.rho_ref - ro)) / ro;
+    if (unknown[3]) g[3] = g[1] - (2.0f / 3.0f) * ro * U;
+    if (unknown[7]) g[7] = g[5] + 0.5f * (g[2] - g[4]) - ro * U * (1.0f / 6.0f);
+    if (unknown[6]) g[6] = g[8] - 0.5f * (g[2] - g[4]) - ro * U * (1.0f / 6.0f);
+  }
+}
+
+__device__ __forceinline__ float sum9(const float g[9]) {
+  return ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
+}
+
+// ---------------------------------------------------------------------------
+// Forces of Eqs. 9, 14, 15 from the psi of the 8 neighbours.
+// psin[i]: psi of neighbour i (ignored when solid[i]); psi_c: own psi.
+// Returns F and |F_m|^2 / psi^2 = G^2 |sum w psi e|^2.
+// ---------------------------------------------------------------------------
+struct Force {
+  float Fx, Fy, fm2;
+};
+
+__device__ __forceinline__ Force interaction_force(const DevParams &p, float psi_c, float psi_w,
+                                                   const float psin[9], unsigned solid_mask) {
+  float qx = 0.f, qy = 0.f, sx = 0.f, sy = 0.f;
+#pragma unroll
+  for (int i = 1; i < 9; i++) {
+    if (solid_mask & (1u << i)) {
+      sx += wpsi(i) * ex(i);
+      sy += wpsi(i) * ey(i);
+    } else {
+      qx += wpsi(i) * psin[i] * ex(i);
+      qy += wpsi(i) * psin[i] * ey(i);
+    }
+  }
+  Force F;
+  F.Fx = -p.G * psi_c * qx - p.Gw * psi_c * psi_w * sx;
+  F.Fy = -p.G * psi_c * qy - p.Gw * psi_c * psi_w * sy;
+  F.fm2 = qx * qx + qy * qy;  // times G^2 inside c_theta_*
+  return F;
+}
+
+// ---------------------------------------------------------------------------
+// Moment-space collision of Eq. 7 with Li's forcing (Eq. 8), written in closed
+// form on the deviation populations.  In: pulled g, total force F, fm2 =
+// |sum w psi e|^2.  Out: post-collision deviations gs.  Returns rho and u.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void collide(const DevParams &p, const float g[9], float Fx, float Fy,
+                                        float fm2, float gs[9], float &rho_out, float &ux_out,
+                                        float &uy_out) {
+  // n = M g (Eq. 6 on deviations; m = n + rho_ref (1, -2, 1, 0, ...))
+  const float sa = g[1] + g[2] + g[3] + g[4];
+  const float sd = g[5] + g[6] + g[7] + g[8];
+  const float drho = g[0] + sa + sd;
+  const float n1 = -4.0f * g[0] - sa + 2.0f * sd;
+  const float n2 = 4.0f * g[0] - 2.0f * sa + sd;
+  const float d57 = g[5] - g[7], d68 = g[6] - g[8];
+  const float jx = g[1] - g[3] + d57 - d68;
+  const float jy = g[2] - g[4] + d57 + d68;
+  const float n4 = -2.0f * (g[1] - g[3]) + d57 - d68;
+  const float n6 = -2.0f * (g[2] - g[4]) + d57 + d68;
+  const float n7 = g[1] - g[2] + g[3] - g[4];
+  const float n8 = g[5] - g[6] + g[7] - g[8];
+
+  const float rho = p.rho_ref + drho;
+  const float inv_rho = 1.0f / rho;
+  const float ux = (jx + 0.5f * Fx) * inv_rho;  // Eq. 13
+  const float uy = (jy + 0.5f * Fy) * inv_rho;
+  const float jxe = rho * ux, jye = rho * uy;
+  const float uu3 = 3.0f * (jxe * ux + jye * uy);  // 3 rho |u|^2
+  const float uF = ux * Fx + uy * Fy;
+
+  float s_nu;
+  if (p.tau_const) {
+    s_nu = p.s_nu_const;
+  } else {
+    float fr = fminf(fmaxf((rho - p.rho_g) * p.inv_drho, 0.0f), 1.0f);
+    s_nu = 1.0f / (p.tau_g + fr * p.dtau);  // Eq. 5
+  }
+
+  // m* - rho_ref c, moment by moment (Eq. 7); (1 - s/2) S from Eq. 8
+  const float m0 = drho;
+  const float m1 = n1 - p.s_e * (n1 + 2.0f * drho - uu3) +
+                   (1.0f - 0.5f * p.s_e) * 6.0f * uF + p.c_theta_e * fm2;
+  const float m2 = n2 - p.s_z * (n2 - drho + uu3) -
+                   (1.0f - 0.5f * p.s_z) * 6.0f * uF - p.c_theta_z * fm2;
+  const float m3 = jx + Fx;
+  const float m4 = n4 - p.s_q * (n4 + jxe) - (1.0f - 0.5f * p.s_q) * Fx;
+  const float m5 = jy + Fy;
+  const float m6 = n6 - p.s_q * (n6 + jye) - (1.0f - 0.5f * p.s_q) * Fy;
+  const float m7 = n7 - s_nu * (n7 - (jxe * ux - jye * uy)) +
+                   (1.0f - 0.5f * s_nu) * 2.0f * (ux * Fx - uy * Fy);
+  const float m8 = n8 - s_nu * (n8 - jxe * uy) + (1.0f - 0.5f * s_nu) * (ux * Fy + uy * Fx);
+
+  // f* = M^-1 m* = M^T D^-1 m*, D = diag(9, 36, 36, 6, 12, 6, 12, 4, 4)
+  const float a0 = m0 * (1.0f / 9.0f), a1 = m1 * (1.0f / 36.0f), a2 = m2 * (1.0f / 36.0f);
+  const float a3 = m3 * (1.0f / 6.0f), a4 = m4 * (1.0f / 12.0f);
+  const float a5 = m5 * (1.0f / 6.0f), a6 = m6 * (1.0f / 12.0f);
+  const float a7 = m7 * 0.25f, a8 = m8 * 0.25f;
+  const float b_ax = a0 - a1 - 2.0f * a2;   // common part of f1..f4
+  const float b_dg = a0 + 2.0f * a1 + a2;   // common part of f5..f8
+  const float px = a3 - 2.0f * a4, py = a5 - 2.0f * a6;
+  const float qx = a3 + a4, qy = a5 + a6;
+  gs[0] = a0 - 4.0f * a1 + 4.0f * a2;
+  gs[1] = b_ax + px + a7;
+  gs[2] = b_ax + py - a7;
+  gs[3] = b_ax - px + a7;
+  gs[4] = b_ax - py - a7;
+  gs[5] = b_dg + qx + qy + a8;
+  gs[6] = b_dg - qx + qy - a8;
+  gs[7] = b_dg - qx - qy + a8;
+  gs[8] = b_dg + qx - qy - a8;
+  rho_out = rho;
+  ux_out = ux;
+  uy_out = uy;
+}
+
+// wall temperature deviation at column x (linear between the two end values)
+__device__ __forceinline__ float wall_T_dev(const DevParams &p, int x) {
+  x = min(max(x, 0), p.nx - 1);
+  return p.tw0 + p.tw_slope * (float)x;
+}
+
+}  // namespace lbm

@@ -1,0 +1,31 @@
+// Kernel launchers shared by the host runtime (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+// split path: three launches per update
+cudaError_t launch_density_psi(const DevParams &p, const float *gs, const float *Tdev, float *rho,
+                               float *psi, unsigned *status, StepScalars sc, cudaStream_t s);
+cudaError_t launch_collide(const DevParams &p, const float *gs, float *gout, const float *Tdev,
+                           const float *psi, float *ux, float *uy, unsigned *status,
+                           StepScalars sc, bool write_populations, cudaStream_t s);
+cudaError_t launch_energy(const DevParams &p, const float *Tin, float *Tout, const float *rho,
+                          const float *ux, const float *uy, unsigned *status, StepScalars sc,
+                          cudaStream_t s);
+
+// fused path: one launch per update
+cudaError_t launch_fused(const DevParams &p, const float *gs, float *gout, const float *Tin,
+                         float *Tout, unsigned *status, StepScalars sc, cudaStream_t s);
+bool fused_supported(const DevParams &p);
+
+// set-up and reductions
+cudaError_t launch_init(const DevParams &p, const double *rho0, float *gout, cudaStream_t s);
+cudaError_t launch_mass_heat(const DevParams &p, const float *rho, const float *Tdev,
+                             double T_ref, double Cv, double *partials, int nblocks,
+                             double *out, cudaStream_t s);
+int mass_heat_blocks(const DevParams &p);
+
+}  // namespace lbm

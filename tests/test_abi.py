@@ -1,0 +1,81 @@
+"""The C ABI library builds, loads without a GPU and exports every entry point
+that include/lbm.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(lbm_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1803_01756_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbm_create", "lbm_step", "lbm_read_fields", "lbm_destroy",
+                     "lbm_write_fields", "lbm_reduce"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1803_01756_gb300 import lattice
+    declared = set(declared_functions())
+    bound = set(lattice.SIGNATURES)
+    assert declared == bound, (declared ^ bound)
+
+
+def test_params_struct_layout_matches_header():
+    """The ctypes mirror lists the struct fields of include/lbm.h in order."""
+    from paper_1803_01756_gb300 import lattice
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    body = re.search(r"typedef struct lbm_params \{(.*?)\} lbm_params_t;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        typ, rest = decl.split(None, 1)
+        for name in rest.split(","):
+            fields.append((typ, name.strip()))
+    mirror = [(f[0], f[1]) for f in lattice.LbmParams._fields_]
+    assert len(fields) == len(mirror)
+    ctype = {"double": ctypes.c_double, "int": ctypes.c_int}
+    for (typ, name), (mname, mtype) in zip(fields, mirror):
+        assert (mname if mname != "lam" else "lambda") == name
+        assert mtype is ctype[typ]
+
+
+def test_host_only_entry_points(lib):
+    from paper_1803_01756_gb300 import lattice
+    L = lattice.load_library()
+    p = lattice.make_params({"eos_a": 2 / 49, "eos_b": 2 / 21, "eos_R": 1.0})
+    assert L.lbm_critical_temperature(ctypes.byref(p)) == pytest.approx(
+        0.0778 * (2 / 49) / (0.45724 * (2 / 21)), rel=1e-15)
+    assert L.lbm_strerror(-4).decode().startswith("device status")
+    h = ctypes.c_void_p()
+    # invalid sizes are rejected before any device call
+    assert L.lbm_create(0, 10, ctypes.byref(p), ctypes.byref(h)) == -1
+    L.lbm_destroy(None)

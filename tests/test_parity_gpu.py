@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA lattice update (through the C ABI) against the FP64
+oracle on identical seeded inputs.
+
+Tolerance: max |X_gpu - X_oracle| / max |X_oracle| <= 1e-5 per field (rho, ux,
+uy, T), the FP32 bound stated for the 200 x 50 channel after 1000 updates.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_01756_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+KERNELS = ["split", "fused"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_01756_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def kernel_id(name):
+    from paper_1803_01756_gb300 import lattice
+    return {"split": lattice.KERNEL_SPLIT, "fused": lattice.KERNEL_FUSED}[name]
+
+
+def make_lattice(nx, ny, p, kernel):
+    from paper_1803_01756_gb300.lattice import Lattice, LbmError
+    try:
+        return Lattice(nx, ny, p, kernel=kernel_id(kernel))
+    except LbmError as e:
+        if kernel == "fused" and e.code == -1:
+            pytest.skip("fused kernel does not cover this configuration")
+        raise
+
+
+def rel_errors(gpu, ref):
+    out = {}
+    for name, a, b in zip(("rho", "ux", "uy", "T"), gpu, ref):
+        scale = np.abs(b).max()
+        out[name] = np.abs(a - b).max() / scale if scale > 0 else np.abs(a - b).max()
+    return out
+
+
+def run_both(nx, ny, p, rho0, steps, kernel, T=None):
+    lat = make_lattice(nx, ny, p, kernel)
+    lat.write_fields(rho0, T)
+    lat.step(steps)
+    gpu = lat.read_fields()
+    lat.close()
+    o = oracle.Oracle(nx, ny, p)
+    o.set_fields(rho0, T)
+    o.step(steps)
+    return gpu, o.fields()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_channel_200x50_1000_steps(kernel):
+    w = inputs.workload("channel_200x50")
+    gpu, ref = run_both(w["nx"], w["ny"], w["params"], inputs.initial_density(w), 1000, kernel)
+    err = rel_errors(gpu, ref)
+    assert max(err.values()) <= TOL, err
+
+
+CASES = [
+    # (nx, ny, overrides) spanning several tiles with ragged edges
+    (37, 13, dict()),
+    (70, 29, dict(x_bc=0)),
+    (45, 33, dict(y_bc=0, x_bc=0)),
+    (53, 17, dict(y_bc=0)),
+    (40, 21, dict(thermal=0)),
+    (40, 21, dict(multiphase=0, gx=1e-5, rho_g=0.0)),
+    (33, 19, dict(Gw=0.2, T_wall_left=0.86, T_wall_right=0.78)),
+    (33, 19, dict(tau_l=0.8, rho_w=1.0, gy=-1e-5, g_omega=0.01)),
+]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("nx,ny,over", CASES)
+def test_small_lattices(nx, ny, over, kernel):
+    p = inputs.base_params(u_amp=0.03, u_period=50.0, **over)
+    rho0 = inputs.noisy_density(nx, ny, inputs.RHO_V_086, 0.01, seed=nx * 1000 + ny)
+    gpu, ref = run_both(nx, ny, p, rho0, 200, kernel)
+    err = rel_errors(gpu, ref)
+    assert max(err.values()) <= TOL, err
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("nx,ny,over", [(2, 9, dict()), (1, 7, dict(x_bc=0)), (9, 1, dict()),
+                                        (5, 2, dict(y_bc=0, x_bc=0)), (64, 3, dict())])
+def test_degenerate_sizes(nx, ny, over, kernel):
+    p = inputs.base_params(**over)
+    rho0 = inputs.noisy_density(nx, ny, inputs.RHO_V_086, 0.01, seed=11)
+    gpu, ref = run_both(nx, ny, p, rho0, 30, kernel)
+    err = rel_errors(gpu, ref)
+    assert max(err.values()) <= TOL, err
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_droplet_with_liquid(kernel):
+    """A liquid droplet (density ratio ~17) on the wall: the liquid exercises the
+    whole EOS range."""
+    nx, ny = 48, 32
+    p = inputs.base_params(x_bc=0, u_amp=0.0)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    r = np.hypot(x - nx / 2, y + 0.5)
+    rho0 = inputs.RHO_V_086 + (inputs.RHO_L_086 - inputs.RHO_V_086) * 0.5 * (1 - np.tanh((r - 10) / 2))
+    gpu, ref = run_both(nx, ny, p, rho0, 300, kernel)
+    err = rel_errors(gpu, ref)
+    assert max(err.values()) <= TOL, err
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_full_size_channel_4096x512(kernel):
+    """The benchmark workload at full size: every node after 3 updates (the oracle
+    takes about a second per update at this size)."""
+    w = inputs.workload("channel_4096x512")
+    gpu, ref = run_both(w["nx"], w["ny"], w["params"], inputs.initial_density(w), 3, kernel)
+    err = rel_errors(gpu, ref)
+    assert max(err.values()) <= TOL, err
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_full_size_long_run_properties(kernel):
+    """4096 x 512 after 500 updates: finite fields, no status bits, density inside the
+    EOS range, and the FP64 mass reduction equal to the sum of the density field."""
+    w = inputs.workload("channel_4096x512")
+    lat = make_lattice(w["nx"], w["ny"], w["params"], kernel)
+    lat.write_fields(inputs.initial_density(w))
+    lat.step(500)
+    rho, ux, uy, T = lat.read_fields()
+    mass, heat = lat.reduce()
+    assert lat.status() == 0
+    lat.close()
+    for a in (rho, ux, uy, T):
+        assert np.isfinite(a).all()
+    assert 0 < rho.min() and rho.max() < 1 / w["params"]["eos_b"]
+    assert mass == pytest.approx(rho.sum(), rel=1e-12)
+    assert heat == pytest.approx((rho * w["params"]["Cv"] * T).sum(), rel=1e-6)
+
+
+def test_mass_reduction_matches_oracle():
+    nx, ny = 40, 24
+    p = inputs.base_params(x_bc=0)
+    rho0 = inputs.noisy_density(nx, ny, 0.5, 0.05, seed=5)
+    from paper_1803_01756_gb300.lattice import Lattice
+    lat = Lattice(nx, ny, p)
+    lat.write_fields(rho0)
+    lat.step(100)
+    m, h = lat.reduce()
+    lat.close()
+    o = oracle.Oracle(nx, ny, p)
+    o.set_fields(rho0)
+    o.step(100)
+    mo, ho = o.mass_heat()
+    assert m == pytest.approx(mo, rel=1e-6)
+    assert h == pytest.approx(ho, rel=1e-6)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_checkpoint_resume_is_bitwise(kernel):
+    w = inputs.workload("channel_200x50")
+    rho0 = inputs.initial_density(w)
+    a = make_lattice(w["nx"], w["ny"], w["params"], kernel)
+    a.write_fields(rho0)
+    a.step(70)
+    state = a.read_state()
+    a.step(30)
+    fa = a.read_fields()
+    b = make_lattice(w["nx"], w["ny"], w["params"], kernel)
+    b.write_state(state)
+    assert b.t == 70
+    b.step(30)
+    fb = b.read_fields()
+    for x, y in zip(fa, fb):
+        assert np.array_equal(x, y)
+    with pytest.raises(Exception):
+        b.write_state(state[:100])
+    a.close()
+    b.close()
+
+
+def test_unstable_parameters_raise_and_keep_the_handle():
+    """lambda / (rho Cv) far beyond the RK4 stability bound: the device status bits
+    are reported as LBM_ERR_UNSTABLE; the handle remains readable."""
+    from paper_1803_01756_gb300.lattice import Lattice, LbmError
+    nx, ny = 16, 8
+    p = inputs.base_params(x_bc=0, **{"lambda": 40.0})
+    lat = Lattice(nx, ny, p)
+    rho0 = inputs.noisy_density(nx, ny, inputs.RHO_V_086, 0.01, seed=2)
+    lat.write_fields(rho0)
+    lat.step(400)
+    with pytest.raises(LbmError) as ei:
+        lat.read_fields()
+    assert ei.value.code == -4
+    assert lat.status() != 0
+    lat.read_fields(check=False)
+    lat.close()
+
+
+def test_runs_on_a_side_stream():
+    import torch
+    from paper_1803_01756_gb300.lattice import Lattice
+    w = inputs.workload("channel_200x50")
+    rho0 = inputs.initial_density(w)
+    s = torch.cuda.Stream()
+    a = Lattice(w["nx"], w["ny"], w["params"])
+    a.write_fields(rho0, stream=s)
+    a.step(50, stream=s)
+    fa = a.read_fields(stream=s)
+    b = Lattice(w["nx"], w["ny"], w["params"])
+    b.write_fields(rho0)
+    b.step(50)
+    fb = b.read_fields()
+    for x, y in zip(fa, fb):
+        assert np.array_equal(x, y)
