@@ -45,6 +45,7 @@ struct lbm_lattice {
   double Tc = 0, T_ref = 0, rho_ref = 0;
   long long t = 0;
   int kernel = LBM_KERNEL_SPLIT;
+  int fused_rows = 0;  // output rows per CTA chunk of the fused kernel
   int cur = 0;   // g[cur]: post-collision populations of the previous update
   int tcur = 0;  // T[tcur]: temperature deviation of time t
   float *g[2] = {nullptr, nullptr};
@@ -116,7 +117,9 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
   d.thermal = p.thermal != 0;
   Tc = critical_temperature(p);
   T_ref = p.T0 * Tc;
-  rho_ref = p.rho_ref > 0.0 ? p.rho_ref : p.rho_g;
+  // deviation reference: given, else the gas density, else the outlet density, else 1
+  rho_ref = p.rho_ref > 0.0 ? p.rho_ref
+                            : (p.rho_g > 0.0 ? p.rho_g : (p.rho_out > 0.0 ? p.rho_out : 1.0));
   d.rho_ref = (float)rho_ref;
   d.T_ref = (float)T_ref;
   d.Tc = (float)Tc;
@@ -128,6 +131,27 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
   d.G = (float)p.G;
   d.Gw = (float)p.Gw;
   d.rho_w = (float)p.rho_w;
+  {
+    // reference state of the deviation pseudopotential, evaluated in double at the
+    // FP32 values of rho_ref and T_ref that the kernels add deviations to
+    const double rr = (double)d.rho_ref, Tr = (double)d.T_ref, b = p.eos_b;
+    const double kap = (double)d.kappa;
+    const double Dr = 1.0 + 2.0 * b * rr - b * b * rr * rr;
+    const double sr = std::sqrt(Tr / Tc);
+    const double rphi = 1.0 + kap * (1.0 - sr);
+    const double P = rr * p.eos_R * Tr / (1.0 - b * rr) - p.eos_a * rphi * rphi * rr * rr / Dr;
+    const double psi2 = p.G != 0.0 ? 2.0 * (P - rr / 3.0) / p.G : 0.0;
+    d.inv_1mbr = (float)(1.0 / (1.0 - b * rr));
+    d.inv_Dr = (float)(1.0 / Dr);
+    d.sr = (float)sr;
+    d.rphi_r = (float)rphi;
+    d.phi_r = (float)(rphi * rphi);
+    d.psi_r2 = (float)(psi2 > 0.0 ? psi2 : 0.0);
+    d.psi_r = (float)std::sqrt(psi2 > 0.0 ? psi2 : 0.0);
+    d.two_over_G = p.G != 0.0 ? (float)(2.0 / p.G) : 0.0f;
+    d.wall_r = (float)((p.G - p.Gw) * std::sqrt(psi2 > 0.0 ? psi2 : 0.0));
+    d.drho_ref_g = (float)(rr - p.rho_g);
+  }
   d.c_theta_e = (float)(12.0 * p.theta * p.s_e * p.G * p.G);
   d.c_theta_z = (float)(12.0 * p.theta * p.s_zeta * p.G * p.G);
   d.s_e = (float)p.s_e;
@@ -143,6 +167,11 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
   d.gy = (float)p.gy;
   d.Cv = (float)p.Cv;
   d.lambda = (float)p.lambda;
+  d.lam_cv = p.Cv > 0.0 ? (float)(p.lambda / p.Cv) : 0.0f;
+  d.R_cv = p.Cv > 0.0 ? (float)(p.eos_R / p.Cv) : 0.0f;
+  d.akap_cv = p.Cv > 0.0 ? (float)(p.eos_a * (0.37464 + 1.54226 * p.eos_omega -
+                                             0.26992 * p.eos_omega * p.eos_omega) / p.Cv)
+                         : 0.0f;
   d.tw0 = (float)(Tc * p.T_wall_left - T_ref);
   d.tw_slope = nx > 1 ? (float)(Tc * (p.T_wall_right - p.T_wall_left) / (nx - 1)) : 0.0f;
   d.T_inlet_dev = (float)(Tc * p.T_inlet - T_ref);
@@ -214,7 +243,7 @@ int one_update(lbm_lattice *h, cudaStream_t s) {
   if (h->kernel == LBM_KERNEL_FUSED) {
     rc = timed(h, KN_FUSED, s, [&] {
       return lbm::launch_fused(d, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur],
-                               h->T[1 - h->tcur], h->status, sc, s);
+                               h->T[1 - h->tcur], h->status, sc, h->fused_rows, s);
     });
     if (rc) return rc;
   } else {
@@ -331,8 +360,10 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
   h->dp = derive(nx, ny, h->pitch, *p, h->Tc, h->T_ref, h->rho_ref);
   h->kernel = LBM_KERNEL_SPLIT;
   if (p->kernel == LBM_KERNEL_FUSED || p->kernel == LBM_KERNEL_AUTO) {
-    if (lbm::fused_supported(h->dp)) h->kernel = LBM_KERNEL_FUSED;
-    else if (p->kernel == LBM_KERNEL_FUSED) {
+    if (lbm::fused_supported(h->dp)) h->fused_rows = lbm::fused_chunk_rows(h->dp, h->device);
+    if (h->fused_rows > 0) {
+      h->kernel = LBM_KERNEL_FUSED;
+    } else if (p->kernel == LBM_KERNEL_FUSED) {
       delete h;
       return LBM_ERR_ARG;
     }

@@ -40,6 +40,16 @@ struct DevParams {
   float Tc, inv_Tc;
   float eos_a, eos_b, eos_R, kappa;
   float G, Gw, rho_w;     // rho_w <= 0: psi_w = local psi
+  // reference state (rho_ref, T_ref) of the deviation pseudopotential
+  float inv_1mbr;         // 1 / (1 - b rho_ref)
+  float inv_Dr;           // 1 / (1 + 2 b rho_ref - b^2 rho_ref^2)
+  float sr;               // sqrt(T_ref / Tc)
+  float rphi_r;           // 1 + kappa (1 - sr)
+  float phi_r;            // rphi_r^2
+  float psi_r, psi_r2;    // psi(rho_ref, T_ref) and its square
+  float two_over_G;
+  float wall_r;           // (G - Gw) psi_r: wall term of Eqs. 9 + 14 at the reference state
+  float drho_ref_g;       // rho_ref - rho_g, the reference part of Eq. 15's (rho - rho_v)
   float c_theta_e;        // 12 theta s_e G^2   ((1 - s_e/2) 12 theta / (tau_e - 1/2) = 12 theta s_e)
   float c_theta_z;        // 12 theta s_zeta G^2
   float s_e, s_z, s_q;
@@ -48,6 +58,7 @@ struct DevParams {
   float s_nu_const;
   float gx, gy;
   float Cv, lambda;
+  float lam_cv, R_cv, akap_cv;  // lambda/Cv, R/Cv, a kappa/Cv
   float tw0, tw_slope;    // wall temperature deviation at x: tw0 + tw_slope * x
   float T_inlet_dev;
   float rho_out;
@@ -89,6 +100,41 @@ __device__ __forceinline__ float pseudopotential(const DevParams &p, float rho, 
   return sqrtf(arg);
 }
 
+// Deviation of psi from psi_r = psi(rho_ref, T_ref), from the deviations
+// drho = rho - rho_ref and dT = T - T_ref.  The pressure difference of Eq. 11 is
+// formed term by term from exact difference identities,
+//   rho/(1-b rho) - rho_r/(1-b rho_r) = drho / ((1-b rho)(1-b rho_r)),
+//   rho^2/D(rho) - rho_r^2/D(rho_r)   = drho (rho + rho_r + 2 b rho rho_r) / (D(rho) D(rho_r)),
+//   phi(T) - phi(T_r) = -kappa (s - s_r) (r + r_r),  s - s_r = dT / (Tc (s + s_r)),
+// so no large nearly equal numbers are subtracted; then
+//   psi^2 - psi_r^2 = 2 (dP - drho/3) / G   and   psi - psi_r = (psi^2 - psi_r^2) / (psi + psi_r).
+// Neighbour differences of psi therefore keep FP32 relative precision.
+__device__ __forceinline__ float pseudopotential_dev(const DevParams &p, float drho, float dT,
+                                                     unsigned &st) {
+  const float rho = p.rho_ref + drho;
+  const float T = p.T_ref + dT;
+  const float br = p.eos_b * rho;
+  const float inv1 = 1.0f / (1.0f - br);
+  const float invD = 1.0f / (1.0f + 2.0f * br - br * br);
+  const float A = rho * inv1;
+  const float B = rho * rho * invD;
+  const float dA = drho * inv1 * p.inv_1mbr;
+  const float dB = drho * (rho + p.rho_ref + 2.0f * br * p.rho_ref) * invD * p.inv_Dr;
+  const float s = sqrtf(T * p.inv_Tc);
+  const float ds = dT * p.inv_Tc / (s + p.sr);
+  const float r = 1.0f + p.kappa * (1.0f - s);
+  const float dphi = -p.kappa * ds * (r + p.rphi_r);
+  const float dP = p.eos_R * (dT * A + p.T_ref * dA) - p.eos_a * (dphi * B + p.phi_r * dB);
+  const float dpsi2 = p.two_over_G * (dP - drho * (1.0f / 3.0f));
+  const float psi2 = p.psi_r2 + dpsi2;
+  if (!(psi2 >= 0.0f)) {
+    st |= ST_PSI_NEG;
+    return -p.psi_r;  // psi = 0
+  }
+  const float den = sqrtf(psi2) + p.psi_r;
+  return den > 0.0f ? dpsi2 / den : 0.0f;
+}
+
 // ---------------------------------------------------------------------------
 // Geometry: classification of the site (x + dx, y + dy) seen from a fluid node
 // ---------------------------------------------------------------------------
@@ -124,9 +170,10 @@ __device__ __forceinline__ int classify(const DevParams &p, int x, int y, int dx
 // wall rows and Zou-He on the open columns (force-free form).
 // gs: post-collision deviations of the previous update.  g: pulled deviations.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void pull(const DevParams &p, const float *__restrict__ gs, int x,
-                                     int y, float u_in, float g[9]) {
+__device__ __forceinline__ void pull_load(const DevParams &p, const float *__restrict__ gs, int x,
+                                          int y, float g[9], unsigned &unknown) {
   const long long c = (long long)y * p.pitch + x;
+  unknown = 0u;
   const bool interior = x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1;
   if (interior) {
 #pragma unroll
@@ -134,54 +181,70 @@ __device__ __forceinline__ void pull(const DevParams &p, const float *__restrict
       g[i] = __ldg(gs + i * p.plane + c - ey(i) * p.pitch - ex(i));
     return;
   }
-  bool unknown[9];
 #pragma unroll
   for (int i = 0; i < 9; i++) {
     int xo, yo;
     int k = classify(p, x, y, -ex(i), -ey(i), xo, yo);
-    unknown[i] = false;
     if (i == 0) {
       g[0] = __ldg(gs + c);
     } else if (k == NB_FLUID) {
       g[i] = __ldg(gs + i * p.plane + (long long)yo * p.pitch + xo);
     } else {
       g[i] = __ldg(gs + opp(i) * p.plane + c);
-      unknown[i] = (k == NB_INLET || k == NB_OUTLET);
+      if (k == NB_INLET || k == NB_OUTLET) unknown |= 1u << i;
     }
   }
-  if (!p.x_open) return;
+}
+
+// Zou-He on the populations that entered from outside the x range (force-free form)
+__device__ __forceinline__ void pull_fix(const DevParams &p, int x, float u_in, float g[9],
+                                         unsigned unknown) {
+  if (!unknown) return;
   if (x == 0) {
     // velocity inlet: f0+f2+f4+2(f3+f6+f7) has weight sum 1 -> rho_ref + deviations
-    float U = u_in;
-    float rb = (g[0] + g[2] + g[4] + 2.0f * (g[3] + g[6] + g[7]) + p.rho_ref) / (1.0f - U);
-    if (unknown[1]) g[1] = g[3] + (2.0f / 3.0f) * rb * U;
-    if (unknown[5]) g[5] = g[7] - 0.5f * (g[2] - g[4]) + rb * U * (1.0f / 6.0f);
-    if (unknown[8]) g[8] = g[6] + 0.5f * (g[2] - g[4]) + rb * U * (1.0f / 6.0f);
+    const float U = u_in;
+    const float rb = (g[0] + g[2] + g[4] + 2.0f * (g[3] + g[6] + g[7]) + p.rho_ref) / (1.0f - U);
+    if (unknown & (1u << 1)) g[1] = g[3] + (2.0f / 3.0f) * rb * U;
+    if (unknown & (1u << 5)) g[5] = g[7] - 0.5f * (g[2] - g[4]) + rb * U * (1.0f / 6.0f);
+    if (unknown & (1u << 8)) g[8] = g[6] + 0.5f * (g[2] - g[4]) + rb * U * (1.0f / 6.0f);
   }
   if (x == p.nx - 1) {
-    float ro = p.rho_out;
-    float U = (g[0] + g[2] + g[4] + 2.0f * (g[1] + g[5] + g[8]) + (p.rho_ref - ro)) / ro;
-    if (unknown[3]) g[3] = g[1] - (2.0f / 3.0f) * ro * U;
-    if (unknown[7]) g[7] = g[5] + 0.5f * (g[2] - g[4]) - ro * U * (1.0f / 6.0f);
-    if (unknown[6]) g[6] = g[8] - 0.5f * (g[2] - g[4]) - ro * U * (1.0f / 6.0f);
+    const float ro = p.rho_out;
+    const float U = (g[0] + g[2] + g[4] + 2.0f * (g[1] + g[5] + g[8]) + (p.rho_ref - ro)) / ro;
+    if (unknown & (1u << 3)) g[3] = g[1] - (2.0f / 3.0f) * ro * U;
+    if (unknown & (1u << 7)) g[7] = g[5] + 0.5f * (g[2] - g[4]) - ro * U * (1.0f / 6.0f);
+    if (unknown & (1u << 6)) g[6] = g[8] - 0.5f * (g[2] - g[4]) - ro * U * (1.0f / 6.0f);
   }
+}
+
+__device__ __forceinline__ void pull(const DevParams &p, const float *__restrict__ gs, int x,
+                                     int y, float u_in, float g[9]) {
+  unsigned unknown;
+  pull_load(p, gs, x, y, g, unknown);
+  pull_fix(p, x, u_in, g, unknown);
 }
 
 __device__ __forceinline__ float sum9(const float g[9]) {
-  return ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
+  return g[0] + (g[1] + g[2] + g[3] + g[4]) + (g[5] + g[6] + g[7] + g[8]);
 }
 
 // ---------------------------------------------------------------------------
-// Forces of Eqs. 9, 14, 15 from the psi of the 8 neighbours.
-// psin[i]: psi of neighbour i (ignored when solid[i]); psi_c: own psi.
-// Returns F and |F_m|^2 / psi^2 = G^2 |sum w psi e|^2.
+// Forces of Eqs. 9, 14 from the psi deviations of the 8 neighbours.
+// dpsin[i]: psi(x+e_i) - psi_r (ignored when solid); dpsi_c: own psi - psi_r.
+// With s = sum_solid w e (so sum_fluid w e = -s) and q = sum_fluid w psi e =
+// sum_fluid w dpsi e - psi_r s, the sum of Eq. 9 and Eq. 14 with the local psi
+// as psi_w is
+//   F = psi_c [ -G sum_fluid w dpsi e + ((G - Gw) psi_r - Gw dpsi_c) s ],
+// written so that no two psi-sized terms cancel in FP32.
+// Returns F and |F_m|^2 / psi^2 = G^2 |q|^2 (G^2 folded into c_theta).
 // ---------------------------------------------------------------------------
 struct Force {
   float Fx, Fy, fm2;
 };
 
-__device__ __forceinline__ Force interaction_force(const DevParams &p, float psi_c, float psi_w,
-                                                   const float psin[9], unsigned solid_mask) {
+__device__ __forceinline__ Force interaction_force(const DevParams &p, float dpsi_c,
+                                                   const float dpsin[9], unsigned solid_mask,
+                                                   float psi_w_fixed) {
   float qx = 0.f, qy = 0.f, sx = 0.f, sy = 0.f;
 #pragma unroll
   for (int i = 1; i < 9; i++) {
@@ -189,14 +252,19 @@ __device__ __forceinline__ Force interaction_force(const DevParams &p, float psi
       sx += wpsi(i) * ex(i);
       sy += wpsi(i) * ey(i);
     } else {
-      qx += wpsi(i) * psin[i] * ex(i);
-      qy += wpsi(i) * psin[i] * ey(i);
+      qx += wpsi(i) * dpsin[i] * ex(i);
+      qy += wpsi(i) * dpsin[i] * ey(i);
     }
   }
+  const float psi_c = p.psi_r + dpsi_c;
+  // wall coefficient: local psi_w by default, a fixed psi(rho_w) when rho_w > 0
+  const float wc = psi_w_fixed > 0.0f ? p.G * p.psi_r - p.Gw * psi_w_fixed
+                                      : p.wall_r - p.Gw * dpsi_c;
   Force F;
-  F.Fx = -p.G * psi_c * qx - p.Gw * psi_c * psi_w * sx;
-  F.Fy = -p.G * psi_c * qy - p.Gw * psi_c * psi_w * sy;
-  F.fm2 = qx * qx + qy * qy;  // times G^2 inside c_theta_*
+  F.Fx = psi_c * (-p.G * qx + wc * sx);
+  F.Fy = psi_c * (-p.G * qy + wc * sy);
+  const float fx = qx - p.psi_r * sx, fy = qy - p.psi_r * sy;
+  F.fm2 = fx * fx + fy * fy;
   return F;
 }
 

@@ -18,8 +18,12 @@ cudaError_t launch_energy(const DevParams &p, const float *Tin, float *Tout, con
 
 // fused path: one launch per update
 cudaError_t launch_fused(const DevParams &p, const float *gs, float *gout, const float *Tin,
-                         float *Tout, unsigned *status, StepScalars sc, cudaStream_t s);
+                         float *Tout, unsigned *status, StepScalars sc, int chunk_rows,
+                         cudaStream_t s);
 bool fused_supported(const DevParams &p);
+// rows per CTA chunk for one wave of resident CTAs on this device (0 on failure);
+// also sets the kernel's shared-memory attribute
+int fused_chunk_rows(const DevParams &p, int device);
 
 // set-up and reductions
 cudaError_t launch_init(const DevParams &p, const double *rho0, float *gout, cudaStream_t s);

@@ -1,6 +1,6 @@
 // Split lattice update: three launches per step.
 //  1. k_density_psi: pull-stream (Eq. 12 with boundary rules), rho (Eq. 13),
-//     pseudopotential (Eqs. 10-11) -> rho, psi arrays.
+//     pseudopotential (Eqs. 10-11) -> rho and psi - psi_r arrays.
 //  2. k_collide: pull-stream again, forces from the psi of the 8 neighbours
 //     (Eqs. 9, 14, 15), velocity (Eq. 13), MRT collision with Li forcing
 //     (Eqs. 6-8) -> post-collision populations and u.
@@ -27,14 +27,14 @@ __global__ void __launch_bounds__(BX *BY)
   unsigned st = 0;
   if (!(rho > 0.0f)) st |= ST_RHO_NONPOS;
   if (p.eos_b * rho >= 1.0f) st |= ST_EOS_POLE;
-  float psi = 0.0f;
+  float dpsi = 0.0f;
   if (p.multiphase) {
-    const float Tabs = p.T_ref + Tdev[c];
-    if (!(Tabs > 0.0f)) st |= ST_T_NONPOS;
-    psi = pseudopotential(p, rho, Tabs, st);
+    const float dT = Tdev[c];
+    if (!(p.T_ref + dT > 0.0f)) st |= ST_T_NONPOS;
+    dpsi = pseudopotential_dev(p, sum9(g), dT, st);
   }
   rho_o[c] = rho;
-  psi_o[c] = psi;
+  psi_o[c] = dpsi;
   set_status(status, st);
 }
 
@@ -51,35 +51,34 @@ __global__ void __launch_bounds__(BX *BY)
   const long long c = (long long)y * p.pitch + x;
   Force F{0.0f, 0.0f, 0.0f};
   if (p.multiphase) {
-    float psin[9];
+    float dpsin[9];
     unsigned solid = 0;
     const bool interior = x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1;
 #pragma unroll
     for (int i = 1; i < 9; i++) {
       if (interior) {
-        psin[i] = psi[c + ey(i) * p.pitch + ex(i)];
+        dpsin[i] = psi[c + ey(i) * p.pitch + ex(i)];
       } else {
         int xo, yo;
         int k = classify(p, x, y, ex(i), ey(i), xo, yo);
         if (k == NB_SOLID) {
           solid |= 1u << i;
-          psin[i] = 0.0f;
+          dpsin[i] = 0.0f;
         } else {
-          psin[i] = psi[(long long)yo * p.pitch + xo];
+          dpsin[i] = psi[(long long)yo * p.pitch + xo];
         }
       }
     }
-    const float psic = psi[c];
-    float psiw = psic;
+    float psiw = 0.0f;
     if (p.rho_w > 0.0f && solid) {
       unsigned st_unused = 0;
       psiw = pseudopotential(p, p.rho_w, p.T_ref + Tdev[c], st_unused);
     }
-    F = interaction_force(p, psic, psiw, psin, solid);
+    F = interaction_force(p, psi[c], dpsin, solid, psiw);
   }
-  const float rho_b = p.rho_ref + sum9(g);
-  F.Fx += (rho_b - p.rho_g) * p.gx * sc.gcos;  // Eq. 15
-  F.Fy += (rho_b - p.rho_g) * p.gy * sc.gcos;
+  const float rho_v = p.drho_ref_g + sum9(g);  // rho - rho_v of Eq. 15
+  F.Fx += rho_v * p.gx * sc.gcos;
+  F.Fy += rho_v * p.gy * sc.gcos;
   float gn[9], rho, ux, uy;
   collide(p, g, F.Fx, F.Fy, F.fm2, gn, rho, ux, uy);
   if (WRITE_POP) {

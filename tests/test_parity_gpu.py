@@ -1,8 +1,11 @@
 """GPU parity: the CUDA lattice update (through the C ABI) against the FP64
 oracle on identical seeded inputs.
 
-Tolerance: max |X_gpu - X_oracle| / max |X_oracle| <= 1e-5 per field (rho, ux,
-uy, T), the FP32 bound stated for the 200 x 50 channel after 1000 updates.
+Tolerance: max |X_gpu - X_oracle| / max |X_oracle| <= 1e-5 per field, the FP32
+bound stated for the 200 x 50 channel after 1000 updates.  The fields are rho,
+the velocity vector u (|.| is the Euclidean norm per node) and T.  The velocity
+scale is floored at U_FLOOR so that nearly quiescent lattices (|u| ~ 1e-7) are
+compared in absolute terms (1e-8 in lattice units) instead of relative to noise.
 """
 import numpy as np
 import pytest
@@ -13,6 +16,7 @@ from paper_1803_01756_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
+U_FLOOR = 1e-3
 KERNELS = ["split", "fused"]
 
 
@@ -42,11 +46,15 @@ def make_lattice(nx, ny, p, kernel):
 
 
 def rel_errors(gpu, ref):
-    out = {}
-    for name, a, b in zip(("rho", "ux", "uy", "T"), gpu, ref):
-        scale = np.abs(b).max()
-        out[name] = np.abs(a - b).max() / scale if scale > 0 else np.abs(a - b).max()
-    return out
+    rho, ux, uy, T = gpu
+    rrho, rux, ruy, rT = ref
+    du = np.hypot(ux - rux, uy - ruy).max()
+    umax = np.hypot(rux, ruy).max()
+    return {
+        "rho": np.abs(rho - rrho).max() / np.abs(rrho).max(),
+        "u": du / max(umax, U_FLOOR),
+        "T": np.abs(T - rT).max() / np.abs(rT).max(),
+    }
 
 
 def run_both(nx, ny, p, rho0, steps, kernel, T=None):
@@ -77,7 +85,7 @@ CASES = [
     (53, 17, dict(y_bc=0)),
     (40, 21, dict(thermal=0)),
     (40, 21, dict(multiphase=0, gx=1e-5, rho_g=0.0)),
-    (33, 19, dict(Gw=0.2, T_wall_left=0.86, T_wall_right=0.78)),
+    (33, 19, dict(Gw=-1.0, T_wall_left=0.86, T_wall_right=0.78)),
     (33, 19, dict(tau_l=0.8, rho_w=1.0, gy=-1e-5, g_omega=0.01)),
 ]
 
