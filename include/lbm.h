@@ -71,7 +71,7 @@ typedef struct lbm_params {
   int thermal;                           /* 1: advance T with Eqs. 16-18 (RK4) */
   int multiphase;                        /* 1: pseudopotential forces, Eqs. 9, 14 */
   int storage;                           /* LBM_STORAGE_* */
-  double rho_ref;                        /* deviation reference density; <= 0: rho_g */
+  double rho_ref;                        /* deviation reference density; <= 0: rho_g, else rho_out, else 1 */
   int kernel;                            /* LBM_KERNEL_* */
 } lbm_params_t;
 
@@ -138,6 +138,7 @@ const char *lbm_strerror(int code);
 
 /* Critical temperature of Eq. 11 for the given parameters. */
 double lbm_critical_temperature(const lbm_params_t *p);
+
 
 #ifdef __cplusplus
 }
