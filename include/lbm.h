@@ -139,6 +139,29 @@ const char *lbm_strerror(int code);
 /* Critical temperature of Eq. 11 for the given parameters. */
 double lbm_critical_temperature(const lbm_params_t *p);
 
+/* Largest nx or ny that lbm_mass_heat_noalloc accepts. */
+#define LBM_NOALLOC_MAX_DIM (1 << 20)
+
+/* FP64 sums of rho and of rho * Cv * (T_dev + T_ref) over an nx * ny field pair, for
+   callers that cannot allocate device memory: a host framework or serving loop that
+   owns the whole device-memory budget and hands out buffers only from its own pool,
+   or a latency-critical loop that must not risk the device-wide synchronisation that
+   cudaMalloc and cudaFree can cause.  This entry point has no counterpart in the paper;
+   it is a service of this library.
+   rho, T_dev: device arrays of FP32, row y at element offset y * pitch (pitch >= nx).
+   out: device memory for two doubles, written with {sum rho, sum rho Cv T}.
+   Enqueued on the stream; nothing is allocated and nothing is synchronised.
+   The two-stage reduction keeps its per-block partial sums in one fixed array of
+   1216 pairs (19 KB) in this library's device memory, which every GPU that loads the
+   library holds until the process exits; the first call on a device looks up that
+   array's address (make that first call before any stream capture).  All calls on a
+   device share the array: calls whose kernels overlap on the GPU (different streams
+   without ordering) race and may return wrong sums.  Each call overwrites every
+   partial pair it reads, so nothing needs clearing between calls.
+   Returns LBM_ERR_ARG for NULL pointers, nx or ny outside [1, LBM_NOALLOC_MAX_DIM] or
+   pitch outside [nx, 2 * LBM_NOALLOC_MAX_DIM]; LBM_ERR_CUDA if a CUDA call fails. */
+int lbm_mass_heat_noalloc(const float *rho, const float *T_dev, int nx, int ny, int pitch,
+                          double T_ref, double Cv, double *out, void *stream);
 
 #ifdef __cplusplus
 }

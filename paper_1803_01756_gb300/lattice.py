@@ -76,6 +76,8 @@ SIGNATURES = {
     "lbm_destroy": ([_vp], None),
     "lbm_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "lbm_critical_temperature": ([ctypes.POINTER(LbmParams)], ctypes.c_double),
+    "lbm_mass_heat_noalloc": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_double, _vp, _vp], ctypes.c_int),
 }
 
 _lib = None
