@@ -165,6 +165,7 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
   d.s_nu_const = (float)(1.0 / p.tau_g);
   d.gx = (float)p.gx;
   d.gy = (float)p.gy;
+  d.has_g = p.gx != 0.0 || p.gy != 0.0;
   d.Cv = (float)p.Cv;
   d.lambda = (float)p.lambda;
   d.lam_cv = p.Cv > 0.0 ? (float)(p.lambda / p.Cv) : 0.0f;

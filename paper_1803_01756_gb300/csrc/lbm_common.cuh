@@ -57,6 +57,7 @@ struct DevParams {
   int tau_const;          // tau_g == tau_l
   float s_nu_const;
   float gx, gy;
+  int has_g;              // gx or gy nonzero
   float Cv, lambda;
   float lam_cv, R_cv, akap_cv;  // lambda/Cv, R/Cv, a kappa/Cv
   float tw0, tw_slope;    // wall temperature deviation at x: tw0 + tw_slope * x

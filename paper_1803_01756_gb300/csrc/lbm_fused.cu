@@ -28,14 +28,15 @@ constexpr int FHALO = 5;             // psi is needed 5 nodes beyond the outputs
 constexpr int FW = FNT - 2 * FHALO;  // output columns per CTA
 
 struct FusedSmem {
-  float psi[4][FNT];                         // psi - psi_r, rows j-3 .. j
-  float ux[4][FNT], uy[4][FNT];              // velocity, rows j-5 .. j-2
-  float cl[4][FNT], cA[4][FNT], cB[4][FNT];  // energy coefficients of rho, same rows
-  float T[8][FNT];                           // T - T_ref, rows j-5 .. j
+  float psi[4][FNT];    // psi - psi_r, rows j-3 .. j
+  float2 u[4][FNT];     // velocity, rows j-5 .. j-2
+  float4 cf[4][FNT];    // energy coefficients of rho (cl, cA, cB, -), same rows
+  float T[8][FNT];      // T - T_ref, rows j-5 .. j
   float T2[4][FNT], T3[4][FNT], T4[4][FNT];  // RK stage fields
-  // own-column values of rows j-10 .. j-4
-  float oux[8][FNT], ouy[8][FNT], ocl[8][FNT], oe1[8][FNT], oe2[8][FNT], oTb[8][FNT],
-      oacc[8][FNT];
+  // own-column values of rows j-10 .. j-4: (ux, uy, cl, e1), (e2, Tb) and the RK4 sum
+  float4 o1[8][FNT];
+  float2 o2[8][FNT];
+  float oacc[8][FNT];
 };
 
 __device__ __forceinline__ int modi(int v, int n) {
@@ -99,12 +100,18 @@ __global__ void __launch_bounds__(FNT, 4)
   for (int i = 0; i < 9; i++) poff[i] = i * (int)p.plane - ey(i) * p.pitch - ex(i);
 
   unsigned st = 0;
+  // running checks folded into status bits once at the end
+  float chk = 0.0f;         // NaN propagates through the sum
+  float rho_min = 1.0f;     // density must stay positive
+  float br_max = 0.0f;      // b rho must stay below the pole of Eq. 11
+  float T_min = 1.0f;       // absolute temperature must stay positive
   float fA[9], fB[9];
 #pragma unroll
   for (int i = 0; i < 9; i++) {
     fA[i] = 0.0f;
     fB[i] = 0.0f;
   }
+  const bool col_interior = cx > 0 && cx < p.nx - 1;
 
   const int J = (ye - Y0) + 3 * FHALO;
 #pragma unroll 1
@@ -118,11 +125,9 @@ __global__ void __launch_bounds__(FNT, 4)
     float fc[9];
     unsigned unk = 0u;
     float Tc = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 9; i++) fc[i] = 0.0f;
     if (s0_row && !r_solid) {
       const int own = ry * p.pitch + cx;
-      if (cx > 0 && cx < p.nx - 1 && ry > 0 && ry < p.ny - 1) {
+      if (col_interior && ry > 0 && ry < p.ny - 1) {
         const float *src = gs + own;
 #pragma unroll
         for (int i = 0; i < 9; i++) fc[i] = __ldg(src + poff[i]);
@@ -139,11 +144,9 @@ __global__ void __launch_bounds__(FNT, 4)
         const int sl = (j - 2) & 3;
         const bool solid = p.y_walls && (q < 0 || q >= p.ny);
         if (solid) {
-          S.ux[sl][t] = 0.0f;
-          S.uy[sl][t] = 0.0f;
+          S.u[sl][t] = make_float2(0.0f, 0.0f);
         } else if (col_in) {
-          S.ux[sl][t] = sc.u_in;
-          S.uy[sl][t] = 0.0f;
+          S.u[sl][t] = make_float2(sc.u_in, 0.0f);
         } else if (!col_out) {
           const int qy = p.y_walls ? q : modi(q, p.ny);
           const float drho = sum9(fB);
@@ -186,9 +189,11 @@ __global__ void __launch_bounds__(FNT, 4)
               F = interaction_force(p, dpc, dn, solid_mask, psiw);
             }
           }
-          const float rho_v = p.drho_ref_g + drho;  // rho - rho_v of Eq. 15
-          F.Fx += rho_v * p.gx * sc.gcos;
-          F.Fy += rho_v * p.gy * sc.gcos;
+          if (p.has_g) {
+            const float rho_v = p.drho_ref_g + drho;  // rho - rho_v of Eq. 15
+            F.Fx += rho_v * p.gx * sc.gcos;
+            F.Fy += rho_v * p.gy * sc.gcos;
+          }
           float ux, uy, inv_rho;
           if (dxo == 0 && q >= Y0 && q < ye) {
             float gn[9], rr;
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(FNT, 4)
             float *dst = gout + (qy * p.pitch + c);
 #pragma unroll
             for (int i = 0; i < 9; i++) dst[i * (int)p.plane] = gn[i];
-            if (!isfinite(rr + ux + uy)) st |= ST_NAN;
+            chk += rr + ux + uy;
             inv_rho = 1.0f / rho;
           } else {
             inv_rho = 1.0f / rho;
@@ -205,12 +210,10 @@ __global__ void __launch_bounds__(FNT, 4)
             ux = (jx + 0.5f * F.Fx) * inv_rho;
             uy = (jy + 0.5f * F.Fy) * inv_rho;
           }
-          S.ux[sl][t] = ux;
-          S.uy[sl][t] = uy;
+          S.u[sl][t] = make_float2(ux, uy);
           const float br = p.eos_b * rho;
-          S.cl[sl][t] = p.lam_cv * inv_rho;
-          S.cA[sl][t] = p.R_cv / (1.0f - br);
-          S.cB[sl][t] = p.akap_cv * rho / (1.0f + 2.0f * br - br * br);
+          S.cf[sl][t] = make_float4(p.lam_cv * inv_rho, p.R_cv / (1.0f - br),
+                                    p.akap_cv * rho / (1.0f + 2.0f * br - br * br), 0.0f);
         }
       }
     }
@@ -228,25 +231,22 @@ __global__ void __launch_bounds__(FNT, 4)
             S.T2[sl][t] = p.T_inlet_dev;
           } else if (!col_out) {
             const int um = (j - 5) & 3, u0 = (j - 4) & 3, up = (j - 3) & 3;
+            const float2 a1 = S.u[u0][tr], a3 = S.u[u0][tl], a2 = S.u[up][t], a4 = S.u[um][t];
+            const float2 a5 = S.u[up][tr], a6 = S.u[up][tl], a7 = S.u[um][tl], a8 = S.u[um][tr];
             // div u = 3 sum w_i u(x+e_i).e_i
-            const float divu =
-                (1.0f / 3.0f) * ((S.ux[u0][tr] - S.ux[u0][tl]) + (S.uy[up][t] - S.uy[um][t])) +
-                (1.0f / 12.0f) * ((S.ux[up][tr] + S.uy[up][tr]) - (S.ux[up][tl] - S.uy[up][tl]) -
-                                  (S.ux[um][tl] + S.uy[um][tl]) + (S.ux[um][tr] - S.uy[um][tr]));
-            const float uxo = S.ux[u0][t], uyo = S.uy[u0][t];
-            const float cl = S.cl[u0][t];
-            const float e1 = S.cA[u0][t] * divu, e2 = S.cB[u0][t] * divu;
+            const float divu = (1.0f / 3.0f) * ((a1.x - a3.x) + (a2.y - a4.y)) +
+                               (1.0f / 12.0f) * ((a5.x + a5.y) - (a6.x - a6.y) -
+                                                 (a7.x + a7.y) + (a8.x - a8.y));
+            const float2 uo = S.u[u0][t];
+            const float4 cf = S.cf[u0][t];
+            const float e1 = cf.y * divu, e2 = cf.z * divu;
             const float Tb = S.T[(j - 4) & 7][t];
             const float h1 = rk_rate(p, S.T[(j - 5) & 7], S.T[(j - 4) & 7], S.T[(j - 3) & 7], tl,
-                                     t, tr, uxo, uyo, cl, e1, e2);
+                                     t, tr, uo.x, uo.y, cf.x, e1, e2);
             S.T2[sl][t] = Tb + 0.5f * h1;
             const int o = (j - 4) & 7;
-            S.oux[o][t] = uxo;
-            S.ouy[o][t] = uyo;
-            S.ocl[o][t] = cl;
-            S.oe1[o][t] = e1;
-            S.oe2[o][t] = e2;
-            S.oTb[o][t] = Tb;
+            S.o1[o][t] = make_float4(uo.x, uo.y, cf.x, e1);
+            S.o2[o][t] = make_float2(e2, Tb);
             S.oacc[o][t] = h1;
           }
         }
@@ -263,10 +263,11 @@ __global__ void __launch_bounds__(FNT, 4)
             S.T3[sl][t] = p.T_inlet_dev;
           } else if (!col_out) {
             const int o = (j - 6) & 7;
+            const float4 w1 = S.o1[o][t];
+            const float2 w2 = S.o2[o][t];
             const float h2 = rk_rate(p, S.T2[(j - 7) & 3], S.T2[(j - 6) & 3], S.T2[(j - 5) & 3], tl,
-                                     t, tr, S.oux[o][t], S.ouy[o][t], S.ocl[o][t], S.oe1[o][t],
-                                     S.oe2[o][t]);
-            S.T3[sl][t] = S.oTb[o][t] + 0.5f * h2;
+                                     t, tr, w1.x, w1.y, w1.z, w1.w, w2.x);
+            S.T3[sl][t] = w2.y + 0.5f * h2;
             S.oacc[o][t] += 2.0f * h2;
           }
         }
@@ -283,10 +284,11 @@ __global__ void __launch_bounds__(FNT, 4)
             S.T4[sl][t] = p.T_inlet_dev;
           } else if (!col_out) {
             const int o = (j - 8) & 7;
+            const float4 w1 = S.o1[o][t];
+            const float2 w2 = S.o2[o][t];
             const float h3 = rk_rate(p, S.T3[(j - 9) & 3], S.T3[(j - 8) & 3], S.T3[(j - 7) & 3], tl,
-                                     t, tr, S.oux[o][t], S.ouy[o][t], S.ocl[o][t], S.oe1[o][t],
-                                     S.oe2[o][t]);
-            S.T4[sl][t] = S.oTb[o][t] + h3;
+                                     t, tr, w1.x, w1.y, w1.z, w1.w, w2.x);
+            S.T4[sl][t] = w2.y + h3;
             S.oacc[o][t] += 2.0f * h3;
           }
         }
@@ -296,12 +298,13 @@ __global__ void __launch_bounds__(FNT, 4)
         const int q = r - 10;
         if (j >= 15 && q < ye && dxo == 0) {
           const int o = (j - 10) & 7;
+          const float4 w1 = S.o1[o][t];
+          const float2 w2 = S.o2[o][t];
           const float h4 = rk_rate(p, S.T4[(j - 11) & 3], S.T4[(j - 10) & 3], S.T4[(j - 9) & 3],
-                                   tl, t, tr, S.oux[o][t], S.ouy[o][t], S.ocl[o][t], S.oe1[o][t],
-                                   S.oe2[o][t]);
-          const float Tn = S.oTb[o][t] + (S.oacc[o][t] + h4) * (1.0f / 6.0f);
-          if (!isfinite(Tn)) st |= ST_NAN;
-          if (!(p.T_ref + Tn > 0.0f)) st |= ST_T_NONPOS;
+                                   tl, t, tr, w1.x, w1.y, w1.z, w1.w, w2.x);
+          const float Tn = w2.y + (S.oacc[o][t] + h4) * (1.0f / 6.0f);
+          chk += Tn;
+          T_min = fminf(T_min, p.T_ref + Tn);
           Tout[q * p.pitch + c] = Tn;
         }
       }
@@ -322,9 +325,10 @@ __global__ void __launch_bounds__(FNT, 4)
         S.psi[sl][t] = dpsi;
         if (!col_in && !col_out) {
           const float rho = p.rho_ref + drho;
-          if (!(rho > 0.0f)) st |= ST_RHO_NONPOS;
-          if (p.eos_b * rho >= 1.0f) st |= ST_EOS_POLE;
-          if (!(p.T_ref + Tc > 0.0f)) st |= ST_T_NONPOS;
+          rho_min = fminf(rho_min, rho);
+          br_max = fmaxf(br_max, p.eos_b * rho);
+          T_min = fminf(T_min, p.T_ref + Tc);
+          chk += rho;
         }
       }
     }
@@ -335,6 +339,10 @@ __global__ void __launch_bounds__(FNT, 4)
     }
     __syncthreads();
   }
+  if (!isfinite(chk)) st |= ST_NAN;
+  if (!(rho_min > 0.0f)) st |= ST_RHO_NONPOS;
+  if (!(br_max < 1.0f)) st |= ST_EOS_POLE;
+  if (!(T_min > 0.0f)) st |= ST_T_NONPOS;
   set_status(status, st);
 }
 

@@ -4,8 +4,9 @@ oracle on identical seeded inputs.
 Tolerance: max |X_gpu - X_oracle| / max |X_oracle| <= 1e-5 per field, the FP32
 bound stated for the 200 x 50 channel after 1000 updates.  The fields are rho,
 the velocity vector u (|.| is the Euclidean norm per node) and T.  The velocity
-scale is floored at U_FLOOR so that nearly quiescent lattices (|u| ~ 1e-7) are
-compared in absolute terms (1e-8 in lattice units) instead of relative to noise.
+scale is floored at U_FLOOR = 0.01, half the smallest inlet amplitude of the channel
+workloads, so that slow or quiescent lattices (|u| down to 1e-7) are compared in
+absolute terms (1e-7 in lattice units) instead of relative to their own noise.
 """
 import numpy as np
 import pytest
@@ -16,7 +17,7 @@ from paper_1803_01756_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-U_FLOOR = 1e-3
+U_FLOOR = 1e-2
 KERNELS = ["split", "fused"]
 
 
