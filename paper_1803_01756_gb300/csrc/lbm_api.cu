@@ -154,6 +154,20 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
   }
   d.c_theta_e = (float)(12.0 * p.theta * p.s_e * p.G * p.G);
   d.c_theta_z = (float)(12.0 * p.theta * p.s_zeta * p.G * p.G);
+  {
+    const double se = p.s_e, sz = p.s_zeta, sq = p.s_q;
+    const double cte = 12.0 * p.theta * se * p.G * p.G, ctz = 12.0 * p.theta * sz * p.G * p.G;
+    const double k1[5] = {(1.0 - se) / 36.0, -2.0 * se / 36.0, se / 36.0,
+                          (1.0 - 0.5 * se) * 6.0 / 36.0, cte / 36.0};
+    const double k2[5] = {(1.0 - sz) / 36.0, sz / 36.0, -sz / 36.0,
+                          -(1.0 - 0.5 * sz) * 6.0 / 36.0, -ctz / 36.0};
+    const double kq[3] = {(1.0 - sq) / 12.0, -sq / 12.0, -(1.0 - 0.5 * sq) / 12.0};
+    for (int i = 0; i < 5; i++) {
+      d.k1[i] = (float)k1[i];
+      d.k2[i] = (float)k2[i];
+    }
+    for (int i = 0; i < 3; i++) d.kq[i] = (float)kq[i];
+  }
   d.s_e = (float)p.s_e;
   d.s_z = (float)p.s_zeta;
   d.s_q = (float)p.s_q;

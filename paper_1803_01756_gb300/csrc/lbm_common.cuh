@@ -53,6 +53,11 @@ struct DevParams {
   float c_theta_e;        // 12 theta s_e G^2   ((1 - s_e/2) 12 theta / (tau_e - 1/2) = 12 theta s_e)
   float c_theta_z;        // 12 theta s_zeta G^2
   float s_e, s_z, s_q;
+  // collision coefficients with the 1/D_k of M^-1 = M^T D^-1 folded in (Eqs. 7-8):
+  //   a1 = m1*/36 = k1[0] n1 + k1[1] drho + k1[2] 3rho|u|^2 + k1[3] u.F + k1[4] |q|^2
+  //   a2 = m2*/36 = k2[0] n2 + k2[1] drho + k2[2] 3rho|u|^2 + k2[3] u.F + k2[4] |q|^2
+  //   a4 = m4*/12 = kq[0] n4 + kq[1] rho u_x + kq[2] F_x   (same for a6 with y)
+  float k1[5], k2[5], kq[3];
   float tau_g, dtau, rho_g, inv_drho;  // Eq. 5: tau_g + clamp((rho - rho_g) inv_drho) dtau
   int tau_const;          // tau_g == tau_l
   float s_nu_const;
@@ -307,25 +312,20 @@ __device__ __forceinline__ void collide(const DevParams &p, const float g[9], fl
     s_nu = 1.0f / (p.tau_g + fr * p.dtau);  // Eq. 5
   }
 
-  // m* - rho_ref c, moment by moment (Eq. 7); (1 - s/2) S from Eq. 8
-  const float m0 = drho;
-  const float m1 = n1 - p.s_e * (n1 + 2.0f * drho - uu3) +
-                   (1.0f - 0.5f * p.s_e) * 6.0f * uF + p.c_theta_e * fm2;
-  const float m2 = n2 - p.s_z * (n2 - drho + uu3) -
-                   (1.0f - 0.5f * p.s_z) * 6.0f * uF - p.c_theta_z * fm2;
-  const float m3 = jx + Fx;
-  const float m4 = n4 - p.s_q * (n4 + jxe) - (1.0f - 0.5f * p.s_q) * Fx;
-  const float m5 = jy + Fy;
-  const float m6 = n6 - p.s_q * (n6 + jye) - (1.0f - 0.5f * p.s_q) * Fy;
-  const float m7 = n7 - s_nu * (n7 - (jxe * ux - jye * uy)) +
-                   (1.0f - 0.5f * s_nu) * 2.0f * (ux * Fx - uy * Fy);
-  const float m8 = n8 - s_nu * (n8 - jxe * uy) + (1.0f - 0.5f * s_nu) * (ux * Fy + uy * Fx);
-
-  // f* = M^-1 m* = M^T D^-1 m*, D = diag(9, 36, 36, 6, 12, 6, 12, 4, 4)
-  const float a0 = m0 * (1.0f / 9.0f), a1 = m1 * (1.0f / 36.0f), a2 = m2 * (1.0f / 36.0f);
-  const float a3 = m3 * (1.0f / 6.0f), a4 = m4 * (1.0f / 12.0f);
-  const float a5 = m5 * (1.0f / 6.0f), a6 = m6 * (1.0f / 12.0f);
-  const float a7 = m7 * 0.25f, a8 = m8 * 0.25f;
+  // m* - rho_ref c, moment by moment (Eq. 7) with (1 - s/2) S from Eq. 8, each already
+  // divided by its D_k: a_k = (m*_k - rho_ref c_k) / D_k
+  const float a0 = drho * (1.0f / 9.0f);
+  const float a1 = p.k1[0] * n1 + p.k1[1] * drho + p.k1[2] * uu3 + p.k1[3] * uF + p.k1[4] * fm2;
+  const float a2 = p.k2[0] * n2 + p.k2[1] * drho + p.k2[2] * uu3 + p.k2[3] * uF + p.k2[4] * fm2;
+  const float a3 = (jx + Fx) * (1.0f / 6.0f);
+  const float a4 = p.kq[0] * n4 + p.kq[1] * jxe + p.kq[2] * Fx;
+  const float a5 = (jy + Fy) * (1.0f / 6.0f);
+  const float a6 = p.kq[0] * n6 + p.kq[1] * jye + p.kq[2] * Fy;
+  const float a7 = 0.25f * ((1.0f - s_nu) * n7 + s_nu * (jxe * ux - jye * uy) +
+                            (2.0f - s_nu) * (ux * Fx - uy * Fy));
+  const float a8 = 0.25f * ((1.0f - s_nu) * n8 + s_nu * (jxe * uy) +
+                            (1.0f - 0.5f * s_nu) * (ux * Fy + uy * Fx));
+  // f* = M^-1 m* = M^T D^-1 m*
   const float b_ax = a0 - a1 - 2.0f * a2;   // common part of f1..f4
   const float b_dg = a0 + 2.0f * a1 + a2;   // common part of f5..f8
   const float px = a3 - 2.0f * a4, py = a5 - 2.0f * a6;

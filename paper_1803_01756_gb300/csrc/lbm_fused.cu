@@ -64,6 +64,9 @@ __device__ __forceinline__ float rk_rate(const DevParams &p, const float *__rest
   return -(ux * gx + uy * gy) + cl * lap - e1 * Tabs - e2 * s * (1.0f + p.kappa - p.kappa * s);
 }
 
+// Boundary modes and physics switches are compile-time parameters:
+// YW walls in y, XO open ends in x, TH energy equation, MP pseudopotential forces.
+template <bool YW, bool XO, bool TH, bool MP>
 __global__ void __launch_bounds__(FNT, 4)
     k_fused_step(DevParams p, const float *__restrict__ gs, float *__restrict__ gout,
                  const float *__restrict__ Tin, float *__restrict__ Tout, unsigned *status,
@@ -80,7 +83,7 @@ __global__ void __launch_bounds__(FNT, 4)
   // column kind: domain (wrapped when periodic) or a ghost beyond an open end
   bool col_in = false, col_out = false;
   int cx;
-  if (!p.x_open) {
+  if (!XO) {
     cx = modi(c, p.nx);
   } else {
     col_in = c < 0;
@@ -91,7 +94,7 @@ __global__ void __launch_bounds__(FNT, 4)
   const int dxo = c < X0 ? X0 - c : (c >= xe ? c - xe + 1 : 0);  // columns outside the outputs
   const int tl = t - 1;
   // the outlet ghost copies column nx-1 for u and temperatures
-  const int tr = (p.x_open && c + 1 >= p.nx) ? (p.nx - 1) - (X0 - FHALO) : t + 1;
+  const int tr = (XO && c + 1 >= p.nx) ? (p.nx - 1) - (X0 - FHALO) : t + 1;
   const float twall = wall_T_dev(p, cx);
 
   // pull offsets of an interior node relative to its own index (Eq. 12, f_i(x) = f*_i(x - e_i))
@@ -120,8 +123,8 @@ __global__ void __launch_bounds__(FNT, 4)
 
     // ---------------- S0 loads: row r ----------------
     const bool s0_row = r < ye + FHALO;
-    const bool r_solid = p.y_walls && (r < 0 || r >= p.ny);
-    const int ry = p.y_walls ? r : modi(r, p.ny);
+    const bool r_solid = YW && (r < 0 || r >= p.ny);
+    const int ry = YW ? r : modi(r, p.ny);
     float fc[9];
     unsigned unk = 0u;
     float Tc = 0.0f;
@@ -142,20 +145,20 @@ __global__ void __launch_bounds__(FNT, 4)
       const int q = r - 2;
       if (j >= 3 && q < ye + 4 && dxo <= 4) {
         const int sl = (j - 2) & 3;
-        const bool solid = p.y_walls && (q < 0 || q >= p.ny);
+        const bool solid = YW && (q < 0 || q >= p.ny);
         if (solid) {
           S.u[sl][t] = make_float2(0.0f, 0.0f);
         } else if (col_in) {
           S.u[sl][t] = make_float2(sc.u_in, 0.0f);
         } else if (!col_out) {
-          const int qy = p.y_walls ? q : modi(q, p.ny);
+          const int qy = YW ? q : modi(q, p.ny);
           const float drho = sum9(fB);
           const float rho = p.rho_ref + drho;
           Force F{0.0f, 0.0f, 0.0f};
-          if (p.multiphase) {
+          if (MP) {
             const int pm = (j - 3) & 3, p0 = (j - 2) & 3, pp = (j - 1) & 3;
-            const bool sdn = p.y_walls && q - 1 < 0;
-            const bool sup = p.y_walls && q + 1 >= p.ny;
+            const bool sdn = YW && q - 1 < 0;
+            const bool sup = YW && q + 1 >= p.ny;
             float dn[9];
             dn[0] = 0.0f;
             dn[1] = S.psi[p0][t + 1];
@@ -218,13 +221,13 @@ __global__ void __launch_bounds__(FNT, 4)
       }
     }
 
-    if (p.thermal) {
+    if (TH) {
       // ---------------- S2: row r-4 (div u, h1) ----------------
       {
         const int q = r - 4;
         if (j >= 6 && q < ye + 3 && dxo <= 3) {
           const int sl = (j - 4) & 3;
-          const bool solid = p.y_walls && (q < 0 || q >= p.ny);
+          const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
             S.T2[sl][t] = twall;
           } else if (col_in) {
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(FNT, 4)
         const int q = r - 6;
         if (j >= 9 && q < ye + 2 && dxo <= 2) {
           const int sl = (j - 6) & 3;
-          const bool solid = p.y_walls && (q < 0 || q >= p.ny);
+          const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
             S.T3[sl][t] = twall;
           } else if (col_in) {
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(FNT, 4)
         const int q = r - 8;
         if (j >= 12 && q < ye + 1 && dxo <= 1) {
           const int sl = (j - 8) & 3;
-          const bool solid = p.y_walls && (q < 0 || q >= p.ny);
+          const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
             S.T4[sl][t] = twall;
           } else if (col_in) {
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(FNT, 4)
         S.T[sT][t] = col_in ? p.T_inlet_dev : Tc;
         float dpsi = 0.0f;
         const float drho = sum9(fc);
-        if (p.multiphase) dpsi = pseudopotential_dev(p, drho, Tc, st);
+        if (MP) dpsi = pseudopotential_dev(p, drho, Tc, st);
         S.psi[sl][t] = dpsi;
         if (!col_in && !col_out) {
           const float rho = p.rho_ref + drho;
@@ -353,13 +356,36 @@ bool fused_supported(const DevParams &p) {
   return p.nx >= 1 && p.ny >= 1 && 9LL * p.plane + p.pitch < 2147483647LL;
 }
 
+namespace {
+
+using FusedFn = void (*)(DevParams, const float *, float *, const float *, float *, unsigned *,
+                         StepScalars, int);
+
+FusedFn fused_variant(const DevParams &p) {
+  static const FusedFn table[16] = {
+      k_fused_step<false, false, false, false>, k_fused_step<false, false, false, true>,
+      k_fused_step<false, false, true, false>,  k_fused_step<false, false, true, true>,
+      k_fused_step<false, true, false, false>,  k_fused_step<false, true, false, true>,
+      k_fused_step<false, true, true, false>,   k_fused_step<false, true, true, true>,
+      k_fused_step<true, false, false, false>,  k_fused_step<true, false, false, true>,
+      k_fused_step<true, false, true, false>,   k_fused_step<true, false, true, true>,
+      k_fused_step<true, true, false, false>,   k_fused_step<true, true, false, true>,
+      k_fused_step<true, true, true, false>,    k_fused_step<true, true, true, true>};
+  const int k = (p.y_walls ? 8 : 0) | (p.x_open ? 4 : 0) | (p.thermal ? 2 : 0) |
+                (p.multiphase ? 1 : 0);
+  return table[k];
+}
+
+}  // namespace
+
 int fused_chunk_rows(const DevParams &p, int device) {
   int sms = 0, occ = 0;
+  const FusedFn fn = fused_variant(p);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-  if (cudaFuncSetAttribute(k_fused_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(FusedSmem)) != cudaSuccess)
     return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_step, FNT, sizeof(FusedSmem)) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, FNT, sizeof(FusedSmem)) !=
           cudaSuccess ||
       occ < 1)
     return 0;
@@ -375,7 +401,7 @@ cudaError_t launch_fused(const DevParams &p, const float *gs, float *gout, const
                          float *Tout, unsigned *status, StepScalars sc, int H, cudaStream_t s) {
   if (H < 1) return cudaErrorInvalidValue;
   dim3 grid((p.nx + FW - 1) / FW, (p.ny + H - 1) / H);
-  k_fused_step<<<grid, FNT, sizeof(FusedSmem), s>>>(p, gs, gout, Tin, Tout, status, sc, H);
+  fused_variant(p)<<<grid, FNT, sizeof(FusedSmem), s>>>(p, gs, gout, Tin, Tout, status, sc, H);
   return cudaGetLastError();
 }
 
