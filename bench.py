@@ -114,8 +114,21 @@ def setup_distributed():
         import torch.distributed as dist
         import torch
         backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
         dist.init_process_group(backend=backend)
     return world, rank, local, dist
+
+
+def max_over_ranks(value: float, dist) -> float:
+    """Largest value over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized():
+        return value
+    import torch
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def time_oracle(w: dict, nx: int, ny: int, steps: int):
@@ -213,10 +226,7 @@ def our_arm(args, world, rank, local, dist):
     elapsed_ms = ev0.elapsed_time(ev1)
     per_kernel = lat.timing_get(stream=stream)
     lat.timing_enable(False)
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist)
     status = lat.status()
 
     cells = nx * ny
@@ -263,10 +273,7 @@ def our_arm(args, world, rank, local, dist):
             assert rc == 0, rc
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, dist)
         e2e = {"value": world * cells * inner * reps / dt / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": 8 * cells / inner,
                "d2h_bytes_per_step": 4 * 4 * info["pitch"] * ny / inner,

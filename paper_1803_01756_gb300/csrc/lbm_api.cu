@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -45,7 +46,7 @@ struct lbm_lattice {
   double Tc = 0, T_ref = 0, rho_ref = 0;
   long long t = 0;
   int kernel = LBM_KERNEL_SPLIT;
-  int fused_rows = 0;  // output rows per CTA chunk of the fused kernel
+  lbm::FusedTiling fused{0, 0};  // CTA tiling of the fused kernel
   int cur = 0;   // g[cur]: post-collision populations of the previous update
   int tcur = 0;  // T[tcur]: temperature deviation of time t
   float *g[2] = {nullptr, nullptr};
@@ -258,7 +259,7 @@ int one_update(lbm_lattice *h, cudaStream_t s) {
   if (h->kernel == LBM_KERNEL_FUSED) {
     rc = timed(h, KN_FUSED, s, [&] {
       return lbm::launch_fused(d, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur],
-                               h->T[1 - h->tcur], h->status, sc, h->fused_rows, s);
+                               h->T[1 - h->tcur], h->status, sc, h->fused, s);
     });
     if (rc) return rc;
   } else {
@@ -375,8 +376,14 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
   h->dp = derive(nx, ny, h->pitch, *p, h->Tc, h->T_ref, h->rho_ref);
   h->kernel = LBM_KERNEL_SPLIT;
   if (p->kernel == LBM_KERNEL_FUSED || p->kernel == LBM_KERNEL_AUTO) {
-    if (lbm::fused_supported(h->dp)) h->fused_rows = lbm::fused_chunk_rows(h->dp, h->device);
-    if (h->fused_rows > 0) {
+    if (lbm::fused_supported(h->dp)) h->fused = lbm::fused_tiling(h->dp, h->device);
+    // LBM_FUSED_TILE="W,H" overrides the tiling (tuning experiments)
+    if (const char *env = std::getenv("LBM_FUSED_TILE")) {
+      int W = 0, H = 0;
+      if (std::sscanf(env, "%d,%d", &W, &H) == 2 && W >= 1 && W <= 118 && H >= 1)
+        h->fused = lbm::FusedTiling{W, H};
+    }
+    if (h->fused.W > 0) {
       h->kernel = LBM_KERNEL_FUSED;
     } else if (p->kernel == LBM_KERNEL_FUSED) {
       delete h;

@@ -60,7 +60,8 @@ __device__ __forceinline__ float rk_rate(const DevParams &p, const float *__rest
   const float lap = (2.0f / 3.0f) * ((v1 + v3) + (v2 + v4) - 4.0f * c) +
                     (1.0f / 6.0f) * ((v5 + v7) + (v6 + v8) - 4.0f * c);
   const float Tabs = p.T_ref + c;
-  const float s = sqrtf(Tabs * p.inv_Tc);
+  const float x = Tabs * p.inv_Tc;  // T > 0 on fluid nodes
+  const float s = x * rsqrtf(x);
   return -(ux * gx + uy * gy) + cl * lap - e1 * Tabs - e2 * s * (1.0f + p.kappa - p.kappa * s);
 }
 
@@ -70,12 +71,12 @@ template <bool YW, bool XO, bool TH, bool MP>
 __global__ void __launch_bounds__(FNT, 4)
     k_fused_step(DevParams p, const float *__restrict__ gs, float *__restrict__ gout,
                  const float *__restrict__ Tin, float *__restrict__ Tout, unsigned *status,
-                 StepScalars sc, int H) {
+                 StepScalars sc, int H, int W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
 
   const int t = threadIdx.x;
-  const int X0 = blockIdx.x * FW;
+  const int X0 = blockIdx.x * W;
   const int Y0 = blockIdx.y * H;
   const int ye = min(Y0 + H, p.ny);
   const int c = X0 - FHALO + t;  // lattice column of this thread
@@ -90,11 +91,12 @@ __global__ void __launch_bounds__(FNT, 4)
     col_out = c >= p.nx;
     cx = min(max(c, 0), p.nx - 1);
   }
-  const int xe = min(X0 + FW, p.nx);
+  const int xe = min(X0 + W, p.nx);
   const int dxo = c < X0 ? X0 - c : (c >= xe ? c - xe + 1 : 0);  // columns outside the outputs
-  const int tl = t - 1;
-  // the outlet ghost copies column nx-1 for u and temperatures
-  const int tr = (XO && c + 1 >= p.nx) ? (p.nx - 1) - (X0 - FHALO) : t + 1;
+  const int tl = t - 1, tr = t + 1;
+  // The outlet ghost column copies column nx-1 for u and the RK4 stage fields: the thread
+  // of column nx-1 writes those values into the ghost slot too (same thread, no race).
+  const bool mirror = XO && c == p.nx - 1;
   const float twall = wall_T_dev(p, cx);
 
   // pull offsets of an interior node relative to its own index (Eq. 12, f_i(x) = f*_i(x - e_i))
@@ -214,6 +216,7 @@ __global__ void __launch_bounds__(FNT, 4)
             uy = (jy + 0.5f * F.Fy) * inv_rho;
           }
           S.u[sl][t] = make_float2(ux, uy);
+          if (mirror) S.u[sl][t + 1] = make_float2(ux, uy);
           const float br = p.eos_b * rho;
           S.cf[sl][t] = make_float4(p.lam_cv * inv_rho, p.R_cv / (1.0f - br),
                                     p.akap_cv * rho / (1.0f + 2.0f * br - br * br), 0.0f);
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(FNT, 4)
             const float h1 = rk_rate(p, S.T[(j - 5) & 7], S.T[(j - 4) & 7], S.T[(j - 3) & 7], tl,
                                      t, tr, uo.x, uo.y, cf.x, e1, e2);
             S.T2[sl][t] = Tb + 0.5f * h1;
+            if (mirror) S.T2[sl][t + 1] = Tb + 0.5f * h1;
             const int o = (j - 4) & 7;
             S.o1[o][t] = make_float4(uo.x, uo.y, cf.x, e1);
             S.o2[o][t] = make_float2(e2, Tb);
@@ -271,6 +275,7 @@ __global__ void __launch_bounds__(FNT, 4)
             const float h2 = rk_rate(p, S.T2[(j - 7) & 3], S.T2[(j - 6) & 3], S.T2[(j - 5) & 3], tl,
                                      t, tr, w1.x, w1.y, w1.z, w1.w, w2.x);
             S.T3[sl][t] = w2.y + 0.5f * h2;
+            if (mirror) S.T3[sl][t + 1] = w2.y + 0.5f * h2;
             S.oacc[o][t] += 2.0f * h2;
           }
         }
@@ -292,6 +297,7 @@ __global__ void __launch_bounds__(FNT, 4)
             const float h3 = rk_rate(p, S.T3[(j - 9) & 3], S.T3[(j - 8) & 3], S.T3[(j - 7) & 3], tl,
                                      t, tr, w1.x, w1.y, w1.z, w1.w, w2.x);
             S.T4[sl][t] = w2.y + h3;
+            if (mirror) S.T4[sl][t + 1] = w2.y + h3;
             S.oacc[o][t] += 2.0f * h3;
           }
         }
@@ -359,7 +365,7 @@ bool fused_supported(const DevParams &p) {
 namespace {
 
 using FusedFn = void (*)(DevParams, const float *, float *, const float *, float *, unsigned *,
-                         StepScalars, int);
+                         StepScalars, int, int);
 
 FusedFn fused_variant(const DevParams &p) {
   static const FusedFn table[16] = {
@@ -378,30 +384,38 @@ FusedFn fused_variant(const DevParams &p) {
 
 }  // namespace
 
-int fused_chunk_rows(const DevParams &p, int device) {
+FusedTiling fused_tiling(const DevParams &p, int device) {
+  FusedTiling best{0, 0};
   int sms = 0, occ = 0;
   const FusedFn fn = fused_variant(p);
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return best;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(FusedSmem)) != cudaSuccess)
-    return 0;
+    return best;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, FNT, sizeof(FusedSmem)) !=
           cudaSuccess ||
       occ < 1)
-    return 0;
+    return best;
+  // Widest strips (fewest halo columns) and one wave of resident CTAs: measured on
+  // the 4096 x 512 channel, equal-work tilings with narrower strips or two waves
+  // were 2-35 % slower than this.
+  const long long slots = (long long)sms * occ;
   const int strips = (p.nx + FW - 1) / FW;
-  int chunks = (sms * occ) / strips;  // one wave of resident CTAs
+  long long chunks = slots / strips;
   if (chunks < 1) chunks = 1;
-  int H = (p.ny + chunks - 1) / chunks;
-  if (H < 16) H = 16;  // keep the 10-row sweep overhead bounded
-  return H;
+  int H = (int)((p.ny + chunks - 1) / chunks);
+  if (H < 16) H = 16;
+  best = FusedTiling{FW, H};
+  return best;
 }
 
 cudaError_t launch_fused(const DevParams &p, const float *gs, float *gout, const float *Tin,
-                         float *Tout, unsigned *status, StepScalars sc, int H, cudaStream_t s) {
-  if (H < 1) return cudaErrorInvalidValue;
-  dim3 grid((p.nx + FW - 1) / FW, (p.ny + H - 1) / H);
-  fused_variant(p)<<<grid, FNT, sizeof(FusedSmem), s>>>(p, gs, gout, Tin, Tout, status, sc, H);
+                         float *Tout, unsigned *status, StepScalars sc, FusedTiling tl,
+                         cudaStream_t s) {
+  if (tl.H < 1 || tl.W < 1 || tl.W > FW) return cudaErrorInvalidValue;
+  dim3 grid((p.nx + tl.W - 1) / tl.W, (p.ny + tl.H - 1) / tl.H);
+  fused_variant(p)<<<grid, FNT, sizeof(FusedSmem), s>>>(p, gs, gout, Tin, Tout, status, sc, tl.H,
+                                                        tl.W);
   return cudaGetLastError();
 }
 

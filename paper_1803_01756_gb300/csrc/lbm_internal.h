@@ -17,13 +17,17 @@ cudaError_t launch_energy(const DevParams &p, const float *Tin, float *Tout, con
                           cudaStream_t s);
 
 // fused path: one launch per update
+struct FusedTiling {
+  int W;  // output columns per CTA (at most 118)
+  int H;  // output rows per CTA
+};
 cudaError_t launch_fused(const DevParams &p, const float *gs, float *gout, const float *Tin,
-                         float *Tout, unsigned *status, StepScalars sc, int chunk_rows,
+                         float *Tout, unsigned *status, StepScalars sc, FusedTiling tiling,
                          cudaStream_t s);
 bool fused_supported(const DevParams &p);
-// rows per CTA chunk for one wave of resident CTAs on this device (0 on failure);
-// also sets the kernel's shared-memory attribute
-int fused_chunk_rows(const DevParams &p, int device);
+// tiling for one wave of resident CTAs on this device ({0, 0} on failure); also sets
+// the kernel's shared-memory attribute
+FusedTiling fused_tiling(const DevParams &p, int device);
 
 // set-up and reductions
 cudaError_t launch_init(const DevParams &p, const double *rho0, float *gout, cudaStream_t s);
