@@ -188,6 +188,9 @@ def our_arm(args, world, rank, local, dist):
     w = inputs.workload(args.workload)
     nx, ny = w["nx"], w["ny"]
     kernel = {"auto": L.KERNEL_AUTO, "split": L.KERNEL_SPLIT, "fused": L.KERNEL_FUSED}[args.kernel]
+    storage = {"f32": 0, "bf16": 1, "f16": 2}[args.storage]
+    # algorithmic bytes per cell-update: populations read and written once, T read and written
+    bytes_cell = 2 * 9 * (4 if args.storage == "f32" else 2) + 8
 
     # CPU baseline first (rank 0, N = 1): the oracle on the host cores, before any
     # GPU work so that nothing forks after CUDA initialisation
@@ -199,7 +202,7 @@ def our_arm(args, world, rank, local, dist):
                "sample": f"{steps} updates of the full {nx}x{ny} channel ({dt:.1f} s, 1 thread)"}
 
     stream = torch.cuda.current_stream()
-    lat = L.Lattice(nx, ny, w["params"], kernel=kernel)
+    lat = L.Lattice(nx, ny, w["params"], kernel=kernel, storage=storage)
     info = lat.info()
     rho0 = inputs.initial_density(w)
     lat.write_fields(rho0)
@@ -237,7 +240,8 @@ def our_arm(args, world, rank, local, dist):
     peak, peak_kind = measured_peaks()
     top = max(per_kernel.items(), key=lambda kv: kv[1][0])
     top_name, (top_ms, top_n) = top
-    bytes_per_launch = SPLIT_KERNEL_BYTES[top_name] * cells
+    per_cell = bytes_cell if top_name == "k_fused_step" else SPLIT_KERNEL_BYTES[top_name]
+    bytes_per_launch = per_cell * cells
     achieved = bytes_per_launch / (top_ms / top_n / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
@@ -287,12 +291,12 @@ def our_arm(args, world, rank, local, dist):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "nx": nx, "ny": ny, "storage": "f32",
+        "config": {"workload": args.workload, "nx": nx, "ny": ny, "storage": args.storage,
                    "kernel": {1: "split", 2: "fused"}[info["kernel"]],
                    "parallelism": f"replicas x{world}",
                    "l2": f"state {info['device_bytes'] / 1e6:.0f} MB > L2 129 MB; no flush",
-                   "bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
-        "hbm_frac_step": value * 1e6 / world * BYTES_PER_CELL_UPDATE / 1e9 / peak,
+                   "bytes_per_cell_update": bytes_cell},
+        "hbm_frac_step": value * 1e6 / world * bytes_cell / 1e9 / peak,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "status_bits": status,
     }
@@ -307,6 +311,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="channel_4096x512", choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
+                    help="population storage (FP32 arithmetic in every case)")
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -44,10 +44,13 @@ extern "C" {
 
 #define LBM_X_PERIODIC 0
 #define LBM_X_INLET_OUTLET 1 /* Zou-He velocity inlet at x=0, density outlet at x=nx-1 */
+#define LBM_X_PRESSURE_INLET 2 /* Zou-He pressure inlet at x=0, density outlet at x=nx-1 */
 #define LBM_Y_PERIODIC 0
 #define LBM_Y_WALLS 1        /* half-way bounce-back walls below y=0 and above y=ny-1 */
 
 #define LBM_STORAGE_F32 0    /* populations stored as FP32 f_i - w_i rho_ref */
+#define LBM_STORAGE_BF16 1   /* stored as BF16 f_i / w_i - rho_ref (FP32 arithmetic) */
+#define LBM_STORAGE_F16 2    /* stored as FP16 f_i / w_i - rho_ref (FP32 arithmetic) */
 
 #define LBM_KERNEL_AUTO 0
 #define LBM_KERNEL_SPLIT 1   /* density/psi, collide, energy: three launches per update */
@@ -73,6 +76,9 @@ typedef struct lbm_params {
   int storage;                           /* LBM_STORAGE_* */
   double rho_ref;                        /* deviation reference density; <= 0: rho_g, else rho_out, else 1 */
   int kernel;                            /* LBM_KERNEL_* */
+  double p_amp_frac;                     /* pressure inlet (Section 3.3): p = p0 (1 + p_amp_frac
+                                            sin(2 pi t / u_period)), p0 = P_EOS(rho_out, T_inlet),
+                                            imposed as the vapour-branch density of that pressure */
 } lbm_params_t;
 
 typedef struct lbm_lattice *lbm_h;

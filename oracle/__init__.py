@@ -23,7 +23,7 @@ _LIB = os.path.join(_HERE, "_build", "libpplbm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-X_PERIODIC, X_INLET_OUTLET = 0, 1
+X_PERIODIC, X_INLET_OUTLET, X_PRESSURE_INLET = 0, 1, 2
 Y_PERIODIC, Y_WALLS = 0, 1
 
 
@@ -44,6 +44,7 @@ class OrcParams(ctypes.Structure):
         ("u_amp", ctypes.c_double), ("u_period", ctypes.c_double),
         ("rho_out", ctypes.c_double),
         ("thermal", ctypes.c_int), ("multiphase", ctypes.c_int),
+        ("p_amp_frac", ctypes.c_double),
     ]
 
 
@@ -101,6 +102,8 @@ def lib():
         L.orc_status.argtypes = [vp]
         L.orc_status.restype = ctypes.c_uint
         L.orc_energy_rhs.argtypes = [vp, dp, dp, dp, dp, dp]
+        L.orc_inlet_density.argtypes = [P, ctypes.c_long]
+        L.orc_inlet_density.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -140,6 +143,10 @@ def psi(params: dict, rho: float, T: float):
     neg = ctypes.c_int(0)
     v = lib().orc_psi(ctypes.byref(make_params(params)), rho, T, ctypes.byref(neg))
     return v, bool(neg.value)
+
+
+def inlet_density(params: dict, t: int) -> float:
+    return lib().orc_inlet_density(ctypes.byref(make_params(params)), t)
 
 
 def moment_matrix() -> np.ndarray:

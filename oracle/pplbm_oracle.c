@@ -28,6 +28,11 @@
  *  - Energy-equation ghosts: wall rows hold the wall temperature (linear in x
  *    between the two given end values) and zero velocity; the inlet ghost holds
  *    T_inlet and the inlet velocity; the outlet ghost copies the last column.
+ *  - Pressure inlet (Section 3.3): the inlet pressure p0 (1 + a sin(2 pi t/P)) is
+ *    imposed through the density whose Peng-Robinson pressure at T_inlet equals it,
+ *    taken on the vapour branch (below the first maximum of P(rho)); p0 is the
+ *    pressure of the outlet density at T_inlet.  Its energy-equation ghost copies the
+ *    velocity of the inlet column.
  *  - Time: the populations f^t carry the inlet velocity u_amp sin(2 pi t/P) and
  *    the body force of step t is multiplied by cos(g_omega t).
  */
@@ -284,6 +289,40 @@ static int classify(const orc_lattice *L, int x, int y, int dx, int dy, int *xo,
   return NB_FLUID;
 }
 
+/* first density where dP/drho = 0 at temperature T (the vapour spinodal), or the
+   pole region when the isotherm is monotone */
+static double vapour_branch_end(const orc_params *p, double T) {
+  double h = 1e-7, rmax = 0.999 / p->eos_b, step = 1e-3;
+  double prev = 1e-6;
+  for (double r = 1e-6 + step; r < rmax; r += step) {
+    double d = orc_eos_pressure(p, r + h, T) - orc_eos_pressure(p, r - h, T);
+    if (d <= 0.0) {
+      double lo = prev, hi = r;
+      for (int it = 0; it < 100; it++) {
+        double mid = 0.5 * (lo + hi);
+        double dm = orc_eos_pressure(p, mid + h, T) - orc_eos_pressure(p, mid - h, T);
+        if (dm > 0.0) lo = mid; else hi = mid;
+      }
+      return lo;
+    }
+    prev = r;
+  }
+  return rmax;
+}
+
+double orc_inlet_density(const orc_params *p, long t) {
+  double T = orc_critical_temperature(p) * p->T_inlet;
+  double p0 = orc_eos_pressure(p, p->rho_out, T);
+  double s = p->u_period == 0.0 ? 1.0 : sin(2.0 * PI * (double)t / p->u_period);
+  double target = p0 * (1.0 + p->p_amp_frac * s);
+  double lo = 0.0, hi = vapour_branch_end(p, T);
+  for (int it = 0; it < 200; it++) {
+    double mid = 0.5 * (lo + hi);
+    if (orc_eos_pressure(p, mid, T) < target) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
 static double inlet_velocity(const orc_lattice *L, long t) {
   if (L->p.u_period == 0.0) return L->p.u_amp;
   return L->p.u_amp * sin(2.0 * PI * (double)t / L->p.u_period);
@@ -315,8 +354,15 @@ static void zou_he_column(orc_lattice *L, double *g, int x, long t) {
       if ((k == NB_INLET && x == 0) || (k == NB_OUTLET && x == L->nx - 1)) unknown[i] = 1;
     }
     if (x == 0) {
-      double U = inlet_velocity(L, t);
-      double rb = (f[0] + f[2] + f[4] + 2.0 * (f[3] + f[6] + f[7])) / (1.0 - U);
+      double U, rb;
+      if (L->p.x_bc == ORC_X_PRESSURE_INLET) {
+        /* density given: velocity from the known populations */
+        rb = orc_inlet_density(&L->p, t);
+        U = 1.0 - (f[0] + f[2] + f[4] + 2.0 * (f[3] + f[6] + f[7])) / rb;
+      } else {
+        U = inlet_velocity(L, t);
+        rb = (f[0] + f[2] + f[4] + 2.0 * (f[3] + f[6] + f[7])) / (1.0 - U);
+      }
       if (unknown[1]) f[1] = f[3] + (2.0 / 3.0) * rb * U;
       if (unknown[5]) f[5] = f[7] - 0.5 * (f[2] - f[4]) + rb * U / 6.0;
       if (unknown[8]) f[8] = f[6] + 0.5 * (f[2] - f[4]) + rb * U / 6.0;
@@ -332,7 +378,7 @@ static void zou_he_column(orc_lattice *L, double *g, int x, long t) {
 }
 
 static void apply_open_boundaries(orc_lattice *L, double *g, long t) {
-  if (L->p.x_bc != ORC_X_INLET_OUTLET) return;
+  if (L->p.x_bc == ORC_X_PERIODIC) return;
   zou_he_column(L, g, 0, t);
   zou_he_column(L, g, L->nx - 1, t);
 }
@@ -449,7 +495,11 @@ static void ghost_u(const orc_lattice *L, const double *ux, const double *uy, in
   int xo, yo;
   int k = classify(L, x, y, EX[i], EY[i], &xo, &yo);
   if (k == NB_SOLID) { *vx = 0.0; *vy = 0.0; return; }
-  if (k == NB_INLET) { *vx = inlet_velocity(L, L->t); *vy = 0.0; return; }
+  if (k == NB_INLET && L->p.x_bc == ORC_X_INLET_OUTLET) {
+    *vx = inlet_velocity(L, L->t);
+    *vy = 0.0;
+    return;
+  }
   *vx = ux[yo * L->nx + xo];
   *vy = uy[yo * L->nx + xo];
 }
@@ -521,7 +571,7 @@ static void advance_temperature(orc_lattice *L) {
 
 orc_lattice *orc_create(int nx, int ny, const orc_params *p) {
   if (nx < 1 || ny < 1) return NULL;
-  if (p->x_bc == ORC_X_INLET_OUTLET && nx < 2) return NULL;
+  if (p->x_bc != ORC_X_PERIODIC && nx < 2) return NULL;
   orc_lattice *L = (orc_lattice *)calloc(1, sizeof(orc_lattice));
   size_t N = (size_t)nx * ny;
   L->nx = nx;

@@ -23,6 +23,7 @@ extern "C" {
 /* x boundary modes */
 #define ORC_X_PERIODIC 0
 #define ORC_X_INLET_OUTLET 1 /* Zou-He velocity inlet at x=0, density outlet at x=nx-1 */
+#define ORC_X_PRESSURE_INLET 2 /* Zou-He pressure inlet at x=0, density outlet at x=nx-1 */
 /* y boundary modes */
 #define ORC_Y_PERIODIC 0
 #define ORC_Y_WALLS 1        /* half-way bounce-back walls below y=0 and above y=ny-1 */
@@ -50,6 +51,7 @@ typedef struct orc_params {
   double rho_out;                        /* outlet density */
   int thermal;                           /* 1: advance T by Eqs. 16-18 */
   int multiphase;                        /* 1: pseudopotential forces of Eqs. 9, 14 */
+  double p_amp_frac;                     /* pressure inlet: p = p0 (1 + p_amp_frac sin(2 pi t/u_period)) */
 } orc_params;
 
 typedef struct orc_lattice orc_lattice;
@@ -77,6 +79,10 @@ void orc_collide_node(const orc_params *p, const double f[9], double Fx, double 
 /* isotropic finite-difference stencils used by Eq. 16 on a whole periodic grid */
 void orc_grad_periodic(int nx, int ny, const double *phi, double *gx, double *gy);
 void orc_lap_periodic(int nx, int ny, const double *phi, double *lap);
+
+/* inlet density of the pressure inlet at time t: the vapour-branch root of
+   P_EOS(rho, T_inlet) = p0 (1 + p_amp_frac sin(2 pi t / u_period)), p0 = P_EOS(rho_out, T_inlet) */
+double orc_inlet_density(const orc_params *p, long t);
 
 /* ---- lattice ---- */
 orc_lattice *orc_create(int nx, int ny, const orc_params *p);

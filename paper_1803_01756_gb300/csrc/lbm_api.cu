@@ -44,12 +44,14 @@ struct lbm_lattice {
   lbm_params_t p{};
   DevParams dp{};
   double Tc = 0, T_ref = 0, rho_ref = 0;
+  double rho_branch_end = 0;  // vapour-branch end of the isotherm at T_inlet (pressure inlet)
   long long t = 0;
   int kernel = LBM_KERNEL_SPLIT;
   lbm::FusedTiling fused{0, 0};  // CTA tiling of the fused kernel
   int cur = 0;   // g[cur]: post-collision populations of the previous update
   int tcur = 0;  // T[tcur]: temperature deviation of time t
-  float *g[2] = {nullptr, nullptr};
+  void *g[2] = {nullptr, nullptr};  // populations, storage-typed elements
+  int esize = 4;                    // bytes per stored population
   float *T[2] = {nullptr, nullptr};
   float *rho = nullptr, *psi = nullptr, *ux = nullptr, *uy = nullptr;
   unsigned *status = nullptr;
@@ -90,16 +92,19 @@ bool valid_rate(double s) { return s > 0.0 && s < 2.0; }
 int validate(int nx, int ny, const lbm_params_t &p) {
   if (nx < 1 || ny < 1) return LBM_ERR_ARG;
   if (nx > (1 << 20) || ny > (1 << 20)) return LBM_ERR_ARG;
-  if (p.x_bc != LBM_X_PERIODIC && p.x_bc != LBM_X_INLET_OUTLET) return LBM_ERR_ARG;
+  if (p.x_bc != LBM_X_PERIODIC && p.x_bc != LBM_X_INLET_OUTLET && p.x_bc != LBM_X_PRESSURE_INLET)
+    return LBM_ERR_ARG;
   if (p.y_bc != LBM_Y_PERIODIC && p.y_bc != LBM_Y_WALLS) return LBM_ERR_ARG;
-  if (p.x_bc == LBM_X_INLET_OUTLET && (nx < 2 || !(p.rho_out > 0.0))) return LBM_ERR_ARG;
+  if (p.x_bc != LBM_X_PERIODIC && (nx < 2 || !(p.rho_out > 0.0))) return LBM_ERR_ARG;
+  if (p.x_bc == LBM_X_PRESSURE_INLET && !(std::fabs(p.p_amp_frac) < 1.0)) return LBM_ERR_ARG;
   if (!(p.eos_a > 0.0) || !(p.eos_b > 0.0) || !(p.eos_R > 0.0)) return LBM_ERR_ARG;
   if (p.multiphase && !(p.G != 0.0)) return LBM_ERR_ARG;
   if (p.thermal && !(p.Cv > 0.0)) return LBM_ERR_ARG;
   if (!(p.T0 > 0.0)) return LBM_ERR_ARG;
   if (!(p.tau_g > 0.5) || !(p.tau_l > 0.5)) return LBM_ERR_ARG;
   if (!valid_rate(p.s_e) || !valid_rate(p.s_zeta) || !valid_rate(p.s_q)) return LBM_ERR_ARG;
-  if (p.storage != LBM_STORAGE_F32) return LBM_ERR_ARG;
+  if (p.storage != LBM_STORAGE_F32 && p.storage != LBM_STORAGE_BF16 && p.storage != LBM_STORAGE_F16)
+    return LBM_ERR_ARG;
   if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_FUSED) return LBM_ERR_ARG;
   if (p.u_period < 0.0 || std::fabs(p.u_amp) >= 1.0) return LBM_ERR_ARG;
   return LBM_OK;
@@ -112,7 +117,8 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
   d.ny = ny;
   d.pitch = pitch;
   d.plane = (long long)ny * pitch;
-  d.x_open = p.x_bc == LBM_X_INLET_OUTLET;
+  d.x_open = p.x_bc != LBM_X_PERIODIC;
+  d.p_inlet = p.x_bc == LBM_X_PRESSURE_INLET;
   d.y_walls = p.y_bc == LBM_Y_WALLS;
   d.multiphase = p.multiphase != 0;
   d.thermal = p.thermal != 0;
@@ -195,12 +201,58 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
   return d;
 }
 
+// Peng-Robinson pressure of Eq. 11 (host, double)
+double host_pressure(const lbm_params_t &p, double Tc, double rho, double T) {
+  const double k = 0.37464 + 1.54226 * p.eos_omega - 0.26992 * p.eos_omega * p.eos_omega;
+  const double r = 1.0 + k * (1.0 - std::sqrt(T / Tc));
+  const double br = p.eos_b * rho;
+  return rho * p.eos_R * T / (1.0 - br) - p.eos_a * r * r * rho * rho / (1.0 + 2.0 * br - br * br);
+}
+
+// Upper end of the vapour branch at temperature T: the first density where the isotherm
+// stops rising (its first maximum), or close to the pole when it rises throughout.
+double vapour_branch_end(const lbm_params_t &p, double Tc, double T) {
+  const double rmax = 0.999 / p.eos_b, h = 1e-7;
+  auto rising = [&](double r) {
+    return host_pressure(p, Tc, r + h, T) - host_pressure(p, Tc, r - h, T) > 0.0;
+  };
+  double prev = 1e-6;
+  for (double r = prev + 1e-3; r < rmax; r += 1e-3) {
+    if (!rising(r)) {
+      double lo = prev, hi = r;
+      for (int it = 0; it < 100; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (rising(mid)) lo = mid; else hi = mid;
+      }
+      return lo;
+    }
+    prev = r;
+  }
+  return rmax;
+}
+
+// inlet density of the pressure inlet at time t (bisection on the vapour branch)
+double inlet_density(const lbm_lattice *h, long long t) {
+  const lbm_params_t &p = h->p;
+  const double T = h->Tc * p.T_inlet;
+  const double p0 = host_pressure(p, h->Tc, p.rho_out, T);
+  const double s = p.u_period == 0.0 ? 1.0 : std::sin(2.0 * kPi * (double)t / p.u_period);
+  const double target = p0 * (1.0 + p.p_amp_frac * s);
+  double lo = 0.0, hi = h->rho_branch_end;
+  for (int it = 0; it < 200; it++) {
+    const double mid = 0.5 * (lo + hi);
+    if (host_pressure(p, h->Tc, mid, T) < target) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
 StepScalars scalars_at(const lbm_lattice *h, long long t) {
   StepScalars s;
   double u = h->p.u_period == 0.0 ? h->p.u_amp
                                    : h->p.u_amp * std::sin(2.0 * kPi * (double)t / h->p.u_period);
   s.u_in = (float)u;
   s.gcos = (float)std::cos(h->p.g_omega * (double)t);
+  s.rho_in = h->p.x_bc == LBM_X_PRESSURE_INLET ? (float)inlet_density(h, t) : 0.0f;
   return s;
 }
 
@@ -248,8 +300,8 @@ int timed(lbm_lattice *h, int kind, cudaStream_t s, F &&launch) {
 
 int compute_rho_psi(lbm_lattice *h, cudaStream_t s) {
   StepScalars sc = scalars_at(h, h->t);
-  return cuda_fail(lbm::launch_density_psi(h->dp, h->g[h->cur], h->T[h->tcur], h->rho, h->psi,
-                                           h->status, sc, s));
+  return cuda_fail(lbm::launch_density_psi(h->dp, h->p.storage, h->g[h->cur], h->T[h->tcur],
+                                           h->rho, h->psi, h->status, sc, s));
 }
 
 int one_update(lbm_lattice *h, cudaStream_t s) {
@@ -258,19 +310,19 @@ int one_update(lbm_lattice *h, cudaStream_t s) {
   int rc;
   if (h->kernel == LBM_KERNEL_FUSED) {
     rc = timed(h, KN_FUSED, s, [&] {
-      return lbm::launch_fused(d, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur],
+      return lbm::launch_fused(d, h->p.storage, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur],
                                h->T[1 - h->tcur], h->status, sc, h->fused, s);
     });
     if (rc) return rc;
   } else {
     rc = timed(h, KN_DENSITY, s, [&] {
-      return lbm::launch_density_psi(d, h->g[h->cur], h->T[h->tcur], h->rho, h->psi, h->status,
-                                     sc, s);
+      return lbm::launch_density_psi(d, h->p.storage, h->g[h->cur], h->T[h->tcur], h->rho,
+                                     h->psi, h->status, sc, s);
     });
     if (rc) return rc;
     rc = timed(h, KN_COLLIDE, s, [&] {
-      return lbm::launch_collide(d, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur], h->psi, h->ux,
-                                 h->uy, h->status, sc, true, s);
+      return lbm::launch_collide(d, h->p.storage, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur],
+                                 h->psi, h->ux, h->uy, h->status, sc, true, s);
     });
     if (rc) return rc;
     if (d.thermal) {
@@ -320,7 +372,7 @@ cudaError_t dalloc(lbm_lattice *h, T **ptr, size_t count) {
 int upload_fields(lbm_lattice *h, const double *rho, const double *T, cudaStream_t s) {
   const size_t n = (size_t)h->nx * h->ny;
   LBM_CUDA(cudaMemcpyAsync(h->rho0, rho, n * sizeof(double), cudaMemcpyHostToDevice, s));
-  LBM_CUDA(lbm::launch_init(h->dp, h->rho0, h->g[h->cur], s));
+  LBM_CUDA(lbm::launch_init(h->dp, h->p.storage, h->rho0, h->g[h->cur], s));
   // temperature deviations through the pinned staging buffer
   float *st = h->host_stage;
   LBM_CUDA(cudaStreamSynchronize(s));
@@ -374,9 +426,11 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
   h->plane = (long long)ny * h->pitch;
   h->p = *p;
   h->dp = derive(nx, ny, h->pitch, *p, h->Tc, h->T_ref, h->rho_ref);
+  if (p->x_bc == LBM_X_PRESSURE_INLET)
+    h->rho_branch_end = vapour_branch_end(*p, h->Tc, h->Tc * p->T_inlet);
   h->kernel = LBM_KERNEL_SPLIT;
   if (p->kernel == LBM_KERNEL_FUSED || p->kernel == LBM_KERNEL_AUTO) {
-    if (lbm::fused_supported(h->dp)) h->fused = lbm::fused_tiling(h->dp, h->device);
+    if (lbm::fused_supported(h->dp)) h->fused = lbm::fused_tiling(h->dp, p->storage, h->device);
     // LBM_FUSED_TILE="W,H" overrides the tiling (tuning experiments)
     if (const char *env = std::getenv("LBM_FUSED_TILE")) {
       int W = 0, H = 0;
@@ -393,7 +447,12 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
   h->nblocks = lbm::mass_heat_blocks(h->dp);
   const size_t plane = (size_t)h->plane;
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 2 && e == cudaSuccess; k++) e = dalloc(h, &h->g[k], 9 * plane);
+  h->esize = lbm::storage_bytes(p->storage);
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+    char *ptr = nullptr;
+    e = dalloc(h, &ptr, 9 * plane * (size_t)h->esize);
+    h->g[k] = ptr;
+  }
   for (int k = 0; k < 2 && e == cudaSuccess; k++) e = dalloc(h, &h->T[k], plane);
   if (e == cudaSuccess) e = dalloc(h, &h->rho, plane);
   if (e == cudaSuccess) e = dalloc(h, &h->psi, plane);
@@ -407,7 +466,7 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_sums, 2 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(unsigned));
   // padding columns stay zero forever
-  for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMemset(h->g[k], 0, 9 * plane * sizeof(float));
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMemset(h->g[k], 0, 9 * plane * (size_t)h->esize);
   for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMemset(h->T[k], 0, plane * sizeof(float));
   if (e != cudaSuccess) {
     free_all(h);
@@ -473,8 +532,8 @@ int lbm_read_fields(lbm_h h, double *rho, double *ux, double *uy, double *T, voi
   int rc = compute_rho_psi(h, s);
   if (rc) return rc;
   StepScalars sc = scalars_at(h, h->t);
-  LBM_CUDA(lbm::launch_collide(h->dp, h->g[h->cur], nullptr, h->T[h->tcur], h->psi, h->ux, h->uy,
-                               h->status, sc, false, s));
+  LBM_CUDA(lbm::launch_collide(h->dp, h->p.storage, h->g[h->cur], nullptr, h->T[h->tcur], h->psi,
+                               h->ux, h->uy, h->status, sc, false, s));
   struct Out {
     double *dst;
     const float *src;
@@ -512,7 +571,7 @@ int lbm_reduce(lbm_h h, double *mass, double *heat, void *stream) {
 
 int lbm_state_bytes(lbm_h h, size_t *bytes) {
   if (!h || !bytes) return LBM_ERR_ARG;
-  *bytes = sizeof(StateHeader) + sizeof(float) * (size_t)h->plane * 10;
+  *bytes = sizeof(StateHeader) + (size_t)h->plane * (9 * (size_t)h->esize + sizeof(float));
   return LBM_OK;
 }
 
@@ -531,8 +590,9 @@ int lbm_read_state(lbm_h h, void *buf, size_t bytes, void *stream) {
   hd.t = h->t;
   std::memcpy(buf, &hd, sizeof(hd));
   char *dst = (char *)buf + sizeof(hd);
-  LBM_CUDA(cudaMemcpyAsync(dst, h->g[h->cur], sizeof(float) * 9 * h->plane, cudaMemcpyDeviceToHost, s));
-  LBM_CUDA(cudaMemcpyAsync(dst + sizeof(float) * 9 * h->plane, h->T[h->tcur],
+  const size_t gbytes = (size_t)h->esize * 9 * h->plane;
+  LBM_CUDA(cudaMemcpyAsync(dst, h->g[h->cur], gbytes, cudaMemcpyDeviceToHost, s));
+  LBM_CUDA(cudaMemcpyAsync(dst + gbytes, h->T[h->tcur],
                            sizeof(float) * h->plane, cudaMemcpyDeviceToHost, s));
   LBM_CUDA(cudaStreamSynchronize(s));
   return LBM_OK;
@@ -550,8 +610,9 @@ int lbm_write_state(lbm_h h, const void *buf, size_t bytes, void *stream) {
   LBM_CUDA(cudaSetDevice(h->device));
   cudaStream_t s = (cudaStream_t)stream;
   const char *src = (const char *)buf + sizeof(hd);
-  LBM_CUDA(cudaMemcpyAsync(h->g[h->cur], src, sizeof(float) * 9 * h->plane, cudaMemcpyHostToDevice, s));
-  LBM_CUDA(cudaMemcpyAsync(h->T[h->tcur], src + sizeof(float) * 9 * h->plane,
+  const size_t gbytes = (size_t)h->esize * 9 * h->plane;
+  LBM_CUDA(cudaMemcpyAsync(h->g[h->cur], src, gbytes, cudaMemcpyHostToDevice, s));
+  LBM_CUDA(cudaMemcpyAsync(h->T[h->tcur], src + gbytes,
                            sizeof(float) * h->plane, cudaMemcpyHostToDevice, s));
   LBM_CUDA(cudaStreamSynchronize(s));
   h->t = hd.t;

@@ -11,7 +11,9 @@ constexpr int IBX = 32, IBY = 8;
 // rest equilibrium f_i = w_i rho0(x) at every node: the population that node
 // x + e_i pulls from x holds w_i rho0(x + e_i); populations that no fluid node
 // pulls, and those a wall row returns by bounce-back, hold w_i rho0(x).
-__global__ void k_init(DevParams p, const double *__restrict__ rho0, float *__restrict__ gout) {
+template <class S>
+__global__ void k_init(DevParams p, const double *__restrict__ rho0,
+                       typename S::T *__restrict__ gout) {
   const int x = blockIdx.x * IBX + threadIdx.x, y = blockIdx.y * IBY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   const long long c = (long long)y * p.pitch + x;
@@ -23,7 +25,7 @@ __global__ void k_init(DevParams p, const double *__restrict__ rho0, float *__re
       int xo, yo;
       if (classify(p, x, y, ex(i), ey(i), xo, yo) == NB_FLUID) r = rho0[(long long)yo * p.nx + xo];
     }
-    gout[i * p.plane + c] = (float)((double)wlat(i) * (r - (double)p.rho_ref));
+    gout[i * p.plane + c] = S::pack((float)((double)wlat(i) * (r - (double)p.rho_ref)), i);
   }
 }
 
@@ -95,9 +97,19 @@ __global__ void __launch_bounds__(RT)
 
 }  // namespace
 
-cudaError_t launch_init(const DevParams &p, const double *rho0, float *gout, cudaStream_t s) {
+cudaError_t launch_init(const DevParams &p, int storage, const double *rho0, void *gout,
+                        cudaStream_t s) {
   dim3 grid((p.nx + IBX - 1) / IBX, (p.ny + IBY - 1) / IBY);
-  k_init<<<grid, dim3(IBX, IBY), 0, s>>>(p, rho0, gout);
+  switch (storage) {
+    case STORAGE_BF16:
+      k_init<StoreBF16><<<grid, dim3(IBX, IBY), 0, s>>>(p, rho0, static_cast<__nv_bfloat16 *>(gout));
+      break;
+    case STORAGE_F16:
+      k_init<StoreF16><<<grid, dim3(IBX, IBY), 0, s>>>(p, rho0, static_cast<__half *>(gout));
+      break;
+    default:
+      k_init<StoreF32><<<grid, dim3(IBX, IBY), 0, s>>>(p, rho0, static_cast<float *>(gout));
+  }
   return cudaGetLastError();
 }
 

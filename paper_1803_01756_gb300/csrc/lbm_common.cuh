@@ -4,6 +4,8 @@
 // stored numbers are small and FP32 rounding stays far below the field values.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbm {
@@ -27,6 +29,37 @@ __host__ __device__ constexpr float wpsi(int i) {
   return i == 0 ? 0.0f : (i <= 4 ? 1.0f / 3.0f : 1.0f / 12.0f);
 }
 
+// 1 / w_i
+__host__ __device__ constexpr float inv_wlat(int i) {
+  return i == 0 ? 9.0f / 4.0f : (i <= 4 ? 9.0f : 36.0f);
+}
+
+// Population storage.  Kernels always work on g_i = f_i - w_i rho_ref in FP32.
+//  F32 : stores g_i.
+//  BF16, F16 : store h_i = g_i / w_i = f_i / w_i - rho_ref, so that all nine
+//              directions share one range (16-bit, round to nearest).
+struct StoreF32 {
+  using T = float;
+  static __device__ __forceinline__ float load(const T *p, int) { return __ldg(p); }
+  static __device__ __forceinline__ T pack(float g, int) { return g; }
+};
+struct StoreBF16 {
+  using T = __nv_bfloat16;
+  static __device__ __forceinline__ float load(const T *p, int i) {
+    return wlat(i) * __bfloat162float(__ldg(p));
+  }
+  static __device__ __forceinline__ T pack(float g, int i) {
+    return __float2bfloat16_rn(g * inv_wlat(i));
+  }
+};
+struct StoreF16 {
+  using T = __half;
+  static __device__ __forceinline__ float load(const T *p, int i) {
+    return wlat(i) * __half2float(__ldg(p));
+  }
+  static __device__ __forceinline__ T pack(float g, int i) { return __float2half_rn(g * inv_wlat(i)); }
+};
+
 enum : unsigned {
   ST_NAN = 1u, ST_PSI_NEG = 2u, ST_RHO_NONPOS = 4u, ST_EOS_POLE = 8u, ST_T_NONPOS = 16u
 };
@@ -35,6 +68,7 @@ enum : unsigned {
 struct DevParams {
   int nx, ny, pitch;
   int x_open, y_walls, multiphase, thermal;
+  int p_inlet;            // x = 0 is a pressure (density) inlet instead of a velocity inlet
   long long plane;        // ny * pitch, elements per population plane
   float rho_ref, T_ref;   // deviation references
   float Tc, inv_Tc;
@@ -74,6 +108,7 @@ struct DevParams {
 struct StepScalars {
   float u_in;   // inlet velocity of time t
   float gcos;   // cos(g_omega t)
+  float rho_in; // inlet density of time t (pressure inlet)
 };
 
 __device__ __forceinline__ int wrapi(int v, int n) {
@@ -176,15 +211,16 @@ __device__ __forceinline__ int classify(const DevParams &p, int x, int y, int dx
 // wall rows and Zou-He on the open columns (force-free form).
 // gs: post-collision deviations of the previous update.  g: pulled deviations.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void pull_load(const DevParams &p, const float *__restrict__ gs, int x,
-                                          int y, float g[9], unsigned &unknown) {
+template <class S>
+__device__ __forceinline__ void pull_load(const DevParams &p, const typename S::T *__restrict__ gs,
+                                          int x, int y, float g[9], unsigned &unknown) {
   const long long c = (long long)y * p.pitch + x;
   unknown = 0u;
   const bool interior = x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1;
   if (interior) {
 #pragma unroll
     for (int i = 0; i < 9; i++)
-      g[i] = __ldg(gs + i * p.plane + c - ey(i) * p.pitch - ex(i));
+      g[i] = S::load(gs + i * p.plane + c - ey(i) * p.pitch - ex(i), i);
     return;
   }
 #pragma unroll
@@ -192,24 +228,31 @@ __device__ __forceinline__ void pull_load(const DevParams &p, const float *__res
     int xo, yo;
     int k = classify(p, x, y, -ex(i), -ey(i), xo, yo);
     if (i == 0) {
-      g[0] = __ldg(gs + c);
+      g[0] = S::load(gs + c, 0);
     } else if (k == NB_FLUID) {
-      g[i] = __ldg(gs + i * p.plane + (long long)yo * p.pitch + xo);
+      g[i] = S::load(gs + i * p.plane + (long long)yo * p.pitch + xo, i);
     } else {
-      g[i] = __ldg(gs + opp(i) * p.plane + c);
+      g[i] = S::load(gs + opp(i) * p.plane + c, opp(i));
       if (k == NB_INLET || k == NB_OUTLET) unknown |= 1u << i;
     }
   }
 }
 
 // Zou-He on the populations that entered from outside the x range (force-free form)
-__device__ __forceinline__ void pull_fix(const DevParams &p, int x, float u_in, float g[9],
-                                         unsigned unknown) {
+__device__ __forceinline__ void pull_fix(const DevParams &p, int x, const StepScalars &sc,
+                                         float g[9], unsigned unknown) {
   if (!unknown) return;
   if (x == 0) {
-    // velocity inlet: f0+f2+f4+2(f3+f6+f7) has weight sum 1 -> rho_ref + deviations
-    const float U = u_in;
-    const float rb = (g[0] + g[2] + g[4] + 2.0f * (g[3] + g[6] + g[7]) + p.rho_ref) / (1.0f - U);
+    // f0+f2+f4+2(f3+f6+f7) has weight sum 1 -> rho_ref + deviations
+    const float known = g[0] + g[2] + g[4] + 2.0f * (g[3] + g[6] + g[7]);
+    float U, rb;
+    if (p.p_inlet) {
+      rb = sc.rho_in;  // pressure inlet: density given, velocity from the knowns
+      U = (sc.rho_in - p.rho_ref - known) / sc.rho_in;
+    } else {
+      U = sc.u_in;     // velocity inlet
+      rb = (known + p.rho_ref) / (1.0f - U);
+    }
     if (unknown & (1u << 1)) g[1] = g[3] + (2.0f / 3.0f) * rb * U;
     if (unknown & (1u << 5)) g[5] = g[7] - 0.5f * (g[2] - g[4]) + rb * U * (1.0f / 6.0f);
     if (unknown & (1u << 8)) g[8] = g[6] + 0.5f * (g[2] - g[4]) + rb * U * (1.0f / 6.0f);
@@ -223,11 +266,12 @@ __device__ __forceinline__ void pull_fix(const DevParams &p, int x, float u_in, 
   }
 }
 
-__device__ __forceinline__ void pull(const DevParams &p, const float *__restrict__ gs, int x,
-                                     int y, float u_in, float g[9]) {
+template <class S>
+__device__ __forceinline__ void pull(const DevParams &p, const typename S::T *__restrict__ gs, int x,
+                                     int y, const StepScalars &sc, float g[9]) {
   unsigned unknown;
-  pull_load(p, gs, x, y, g, unknown);
-  pull_fix(p, x, u_in, g, unknown);
+  pull_load<S>(p, gs, x, y, g, unknown);
+  pull_fix(p, x, sc, g, unknown);
 }
 
 __device__ __forceinline__ float sum9(const float g[9]) {

@@ -67,9 +67,10 @@ __device__ __forceinline__ float rk_rate(const DevParams &p, const float *__rest
 
 // Boundary modes and physics switches are compile-time parameters:
 // YW walls in y, XO open ends in x, TH energy equation, MP pseudopotential forces.
-template <bool YW, bool XO, bool TH, bool MP>
+template <bool YW, bool XO, bool TH, bool MP, class ST>
 __global__ void __launch_bounds__(FNT, 4)
-    k_fused_step(DevParams p, const float *__restrict__ gs, float *__restrict__ gout,
+    k_fused_step(DevParams p, const typename ST::T *__restrict__ gs,
+                 typename ST::T *__restrict__ gout,
                  const float *__restrict__ Tin, float *__restrict__ Tout, unsigned *status,
                  StepScalars sc, int H, int W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -97,6 +98,8 @@ __global__ void __launch_bounds__(FNT, 4)
   // The outlet ghost column copies column nx-1 for u and the RK4 stage fields: the thread
   // of column nx-1 writes those values into the ghost slot too (same thread, no race).
   const bool mirror = XO && c == p.nx - 1;
+  // with a pressure inlet the inlet ghost copies the velocity of column 0 the same way
+  const bool mirror_in = XO && p.p_inlet && c == 0;
   const float twall = wall_T_dev(p, cx);
 
   // pull offsets of an interior node relative to its own index (Eq. 12, f_i(x) = f*_i(x - e_i))
@@ -133,11 +136,11 @@ __global__ void __launch_bounds__(FNT, 4)
     if (s0_row && !r_solid) {
       const int own = ry * p.pitch + cx;
       if (col_interior && ry > 0 && ry < p.ny - 1) {
-        const float *src = gs + own;
+        const typename ST::T *src = gs + own;
 #pragma unroll
-        for (int i = 0; i < 9; i++) fc[i] = __ldg(src + poff[i]);
+        for (int i = 0; i < 9; i++) fc[i] = ST::load(src + poff[i], i);
       } else {
-        pull_load(p, gs, cx, ry, fc, unk);
+        pull_load<ST>(p, gs, cx, ry, fc, unk);
       }
       Tc = __ldg(Tin + own);
     }
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(FNT, 4)
         if (solid) {
           S.u[sl][t] = make_float2(0.0f, 0.0f);
         } else if (col_in) {
-          S.u[sl][t] = make_float2(sc.u_in, 0.0f);
+          if (!p.p_inlet) S.u[sl][t] = make_float2(sc.u_in, 0.0f);
         } else if (!col_out) {
           const int qy = YW ? q : modi(q, p.ny);
           const float drho = sum9(fB);
@@ -203,9 +206,9 @@ __global__ void __launch_bounds__(FNT, 4)
           if (dxo == 0 && q >= Y0 && q < ye) {
             float gn[9], rr;
             collide(p, fB, F.Fx, F.Fy, F.fm2, gn, rr, ux, uy);
-            float *dst = gout + (qy * p.pitch + c);
+            typename ST::T *dst = gout + (qy * p.pitch + c);
 #pragma unroll
-            for (int i = 0; i < 9; i++) dst[i * (int)p.plane] = gn[i];
+            for (int i = 0; i < 9; i++) dst[i * (int)p.plane] = ST::pack(gn[i], i);
             chk += rr + ux + uy;
             inv_rho = 1.0f / rho;
           } else {
@@ -217,6 +220,7 @@ __global__ void __launch_bounds__(FNT, 4)
           }
           S.u[sl][t] = make_float2(ux, uy);
           if (mirror) S.u[sl][t + 1] = make_float2(ux, uy);
+          if (mirror_in) S.u[sl][t - 1] = make_float2(ux, uy);
           const float br = p.eos_b * rho;
           S.cf[sl][t] = make_float4(p.lam_cv * inv_rho, p.R_cv / (1.0f - br),
                                     p.akap_cv * rho / (1.0f + 2.0f * br - br * br), 0.0f);
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(FNT, 4)
         S.T[sT][t] = twall;
         S.psi[sl][t] = 0.0f;
       } else {
-        pull_fix(p, cx, sc.u_in, fc, unk);
+        pull_fix(p, cx, sc, fc, unk);
         S.T[sT][t] = col_in ? p.T_inlet_dev : Tc;
         float dpsi = 0.0f;
         const float drho = sum9(fc);
@@ -364,38 +368,55 @@ bool fused_supported(const DevParams &p) {
 
 namespace {
 
-using FusedFn = void (*)(DevParams, const float *, float *, const float *, float *, unsigned *,
-                         StepScalars, int, int);
+template <class ST>
+using FusedFn = void (*)(DevParams, const typename ST::T *, typename ST::T *, const float *,
+                         float *, unsigned *, StepScalars, int, int);
 
-FusedFn fused_variant(const DevParams &p) {
-  static const FusedFn table[16] = {
-      k_fused_step<false, false, false, false>, k_fused_step<false, false, false, true>,
-      k_fused_step<false, false, true, false>,  k_fused_step<false, false, true, true>,
-      k_fused_step<false, true, false, false>,  k_fused_step<false, true, false, true>,
-      k_fused_step<false, true, true, false>,   k_fused_step<false, true, true, true>,
-      k_fused_step<true, false, false, false>,  k_fused_step<true, false, false, true>,
-      k_fused_step<true, false, true, false>,   k_fused_step<true, false, true, true>,
-      k_fused_step<true, true, false, false>,   k_fused_step<true, true, false, true>,
-      k_fused_step<true, true, true, false>,    k_fused_step<true, true, true, true>};
+template <class ST>
+FusedFn<ST> fused_variant(const DevParams &p) {
+  static const FusedFn<ST> table[16] = {
+      k_fused_step<false, false, false, false, ST>, k_fused_step<false, false, false, true, ST>,
+      k_fused_step<false, false, true, false, ST>,  k_fused_step<false, false, true, true, ST>,
+      k_fused_step<false, true, false, false, ST>,  k_fused_step<false, true, false, true, ST>,
+      k_fused_step<false, true, true, false, ST>,   k_fused_step<false, true, true, true, ST>,
+      k_fused_step<true, false, false, false, ST>,  k_fused_step<true, false, false, true, ST>,
+      k_fused_step<true, false, true, false, ST>,   k_fused_step<true, false, true, true, ST>,
+      k_fused_step<true, true, false, false, ST>,   k_fused_step<true, true, false, true, ST>,
+      k_fused_step<true, true, true, false, ST>,    k_fused_step<true, true, true, true, ST>};
   const int k = (p.y_walls ? 8 : 0) | (p.x_open ? 4 : 0) | (p.thermal ? 2 : 0) |
                 (p.multiphase ? 1 : 0);
   return table[k];
 }
 
+template <class ST>
+cudaError_t prepare(const DevParams &p, int *occ) {
+  const FusedFn<ST> fn = fused_variant<ST>(p);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(FusedSmem));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, FNT, sizeof(FusedSmem));
+}
+
+template <class ST>
+cudaError_t launch_t(const DevParams &p, const void *gs, void *gout, const float *Tin, float *Tout,
+                     unsigned *status, StepScalars sc, FusedTiling tl, cudaStream_t s) {
+  dim3 grid((p.nx + tl.W - 1) / tl.W, (p.ny + tl.H - 1) / tl.H);
+  fused_variant<ST>(p)<<<grid, FNT, sizeof(FusedSmem), s>>>(
+      p, static_cast<const typename ST::T *>(gs), static_cast<typename ST::T *>(gout), Tin, Tout,
+      status, sc, tl.H, tl.W);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-FusedTiling fused_tiling(const DevParams &p, int device) {
+FusedTiling fused_tiling(const DevParams &p, int storage, int device) {
   FusedTiling best{0, 0};
   int sms = 0, occ = 0;
-  const FusedFn fn = fused_variant(p);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return best;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(FusedSmem)) != cudaSuccess)
-    return best;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, FNT, sizeof(FusedSmem)) !=
-          cudaSuccess ||
-      occ < 1)
-    return best;
+  cudaError_t e = storage == STORAGE_BF16  ? prepare<StoreBF16>(p, &occ)
+                  : storage == STORAGE_F16 ? prepare<StoreF16>(p, &occ)
+                                           : prepare<StoreF32>(p, &occ);
+  if (e != cudaSuccess || occ < 1) return best;
   // Widest strips (fewest halo columns) and one wave of resident CTAs: measured on
   // the 4096 x 512 channel, equal-work tilings with narrower strips or two waves
   // were 2-35 % slower than this.
@@ -409,14 +430,15 @@ FusedTiling fused_tiling(const DevParams &p, int device) {
   return best;
 }
 
-cudaError_t launch_fused(const DevParams &p, const float *gs, float *gout, const float *Tin,
-                         float *Tout, unsigned *status, StepScalars sc, FusedTiling tl,
-                         cudaStream_t s) {
+cudaError_t launch_fused(const DevParams &p, int storage, const void *gs, void *gout,
+                         const float *Tin, float *Tout, unsigned *status, StepScalars sc,
+                         FusedTiling tl, cudaStream_t s) {
   if (tl.H < 1 || tl.W < 1 || tl.W > FW) return cudaErrorInvalidValue;
-  dim3 grid((p.nx + tl.W - 1) / tl.W, (p.ny + tl.H - 1) / tl.H);
-  fused_variant(p)<<<grid, FNT, sizeof(FusedSmem), s>>>(p, gs, gout, Tin, Tout, status, sc, tl.H,
-                                                        tl.W);
-  return cudaGetLastError();
+  switch (storage) {
+    case STORAGE_BF16: return launch_t<StoreBF16>(p, gs, gout, Tin, Tout, status, sc, tl, s);
+    case STORAGE_F16: return launch_t<StoreF16>(p, gs, gout, Tin, Tout, status, sc, tl, s);
+    default: return launch_t<StoreF32>(p, gs, gout, Tin, Tout, status, sc, tl, s);
+  }
 }
 
 }  // namespace lbm

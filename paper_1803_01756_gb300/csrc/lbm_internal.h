@@ -6,12 +6,18 @@
 
 namespace lbm {
 
-// split path: three launches per update
-cudaError_t launch_density_psi(const DevParams &p, const float *gs, const float *Tdev, float *rho,
-                               float *psi, unsigned *status, StepScalars sc, cudaStream_t s);
-cudaError_t launch_collide(const DevParams &p, const float *gs, float *gout, const float *Tdev,
-                           const float *psi, float *ux, float *uy, unsigned *status,
-                           StepScalars sc, bool write_populations, cudaStream_t s);
+// population storage codes (values of lbm_params_t.storage)
+enum : int { STORAGE_F32 = 0, STORAGE_BF16 = 1, STORAGE_F16 = 2 };
+inline int storage_bytes(int storage) { return storage == STORAGE_F32 ? 4 : 2; }
+
+// split path: three launches per update; population pointers point at `storage` elements
+cudaError_t launch_density_psi(const DevParams &p, int storage, const void *gs, const float *Tdev,
+                               float *rho, float *psi, unsigned *status, StepScalars sc,
+                               cudaStream_t s);
+cudaError_t launch_collide(const DevParams &p, int storage, const void *gs, void *gout,
+                           const float *Tdev, const float *psi, float *ux, float *uy,
+                           unsigned *status, StepScalars sc, bool write_populations,
+                           cudaStream_t s);
 cudaError_t launch_energy(const DevParams &p, const float *Tin, float *Tout, const float *rho,
                           const float *ux, const float *uy, unsigned *status, StepScalars sc,
                           cudaStream_t s);
@@ -21,16 +27,17 @@ struct FusedTiling {
   int W;  // output columns per CTA (at most 118)
   int H;  // output rows per CTA
 };
-cudaError_t launch_fused(const DevParams &p, const float *gs, float *gout, const float *Tin,
-                         float *Tout, unsigned *status, StepScalars sc, FusedTiling tiling,
-                         cudaStream_t s);
+cudaError_t launch_fused(const DevParams &p, int storage, const void *gs, void *gout,
+                         const float *Tin, float *Tout, unsigned *status, StepScalars sc,
+                         FusedTiling tiling, cudaStream_t s);
 bool fused_supported(const DevParams &p);
 // tiling for one wave of resident CTAs on this device ({0, 0} on failure); also sets
 // the kernel's shared-memory attribute
-FusedTiling fused_tiling(const DevParams &p, int device);
+FusedTiling fused_tiling(const DevParams &p, int storage, int device);
 
 // set-up and reductions
-cudaError_t launch_init(const DevParams &p, const double *rho0, float *gout, cudaStream_t s);
+cudaError_t launch_init(const DevParams &p, int storage, const double *rho0, void *gout,
+                        cudaStream_t s);
 cudaError_t launch_mass_heat(const DevParams &p, const float *rho, const float *Tdev,
                              double T_ref, double Cv, double *partials, int nblocks,
                              double *out, cudaStream_t s);

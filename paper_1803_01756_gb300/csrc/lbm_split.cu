@@ -14,14 +14,15 @@ namespace {
 
 constexpr int BX = 32, BY = 8;
 
+template <class S>
 __global__ void __launch_bounds__(BX *BY)
-    k_density_psi(DevParams p, const float *__restrict__ gs, const float *__restrict__ Tdev,
+    k_density_psi(DevParams p, const typename S::T *__restrict__ gs, const float *__restrict__ Tdev,
                   float *__restrict__ rho_o, float *__restrict__ psi_o, unsigned *status,
                   StepScalars sc) {
   const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   float g[9];
-  pull(p, gs, x, y, sc.u_in, g);
+  pull<S>(p, gs, x, y, sc, g);
   const float rho = p.rho_ref + sum9(g);
   const long long c = (long long)y * p.pitch + x;
   unsigned st = 0;
@@ -38,16 +39,16 @@ __global__ void __launch_bounds__(BX *BY)
   set_status(status, st);
 }
 
-template <bool WRITE_POP>
+template <class S, bool WRITE_POP>
 __global__ void __launch_bounds__(BX *BY)
-    k_collide(DevParams p, const float *__restrict__ gs, float *__restrict__ gout,
+    k_collide(DevParams p, const typename S::T *__restrict__ gs, typename S::T *__restrict__ gout,
               const float *__restrict__ Tdev, const float *__restrict__ psi,
               float *__restrict__ ux_o, float *__restrict__ uy_o, unsigned *status,
               StepScalars sc) {
   const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   float g[9];
-  pull(p, gs, x, y, sc.u_in, g);
+  pull<S>(p, gs, x, y, sc, g);
   const long long c = (long long)y * p.pitch + x;
   Force F{0.0f, 0.0f, 0.0f};
   if (p.multiphase) {
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(BX *BY)
   collide(p, g, F.Fx, F.Fy, F.fm2, gn, rho, ux, uy);
   if (WRITE_POP) {
 #pragma unroll
-    for (int i = 0; i < 9; i++) gout[i * p.plane + c] = gn[i];
+    for (int i = 0; i < 9; i++) gout[i * p.plane + c] = S::pack(gn[i], i);
   }
   ux_o[c] = ux;
   uy_o[c] = uy;
@@ -136,6 +137,11 @@ __global__ void __launch_bounds__(ETHREADS)
         T = p.T_inlet_dev;
         vx = sc.u_in;
         load = false;
+        if (p.p_inlet) {  // pressure inlet: the velocity ghost copies column 0
+          const long long c0 = (long long)gy * p.pitch;
+          vx = ux[c0];
+          vy = uy[c0];
+        }
       } else if (gx >= p.nx) {
         kind = K_OUTLET;
         red = i - (gx - (p.nx - 1));
@@ -240,24 +246,54 @@ __global__ void __launch_bounds__(ETHREADS)
   set_status(status, st);
 }
 
-}  // namespace
-
-cudaError_t launch_density_psi(const DevParams &p, const float *gs, const float *Tdev, float *rho,
-                               float *psi, unsigned *status, StepScalars sc, cudaStream_t s) {
+template <class S>
+cudaError_t density_psi_t(const DevParams &p, const void *gs, const float *Tdev, float *rho,
+                          float *psi, unsigned *status, StepScalars sc, cudaStream_t s) {
   dim3 grid((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY);
-  k_density_psi<<<grid, dim3(BX, BY), 0, s>>>(p, gs, Tdev, rho, psi, status, sc);
+  k_density_psi<S><<<grid, dim3(BX, BY), 0, s>>>(p, static_cast<const typename S::T *>(gs), Tdev,
+                                                 rho, psi, status, sc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_collide(const DevParams &p, const float *gs, float *gout, const float *Tdev,
-                           const float *psi, float *ux, float *uy, unsigned *status,
-                           StepScalars sc, bool write_populations, cudaStream_t s) {
+template <class S>
+cudaError_t collide_t(const DevParams &p, const void *gs, void *gout, const float *Tdev,
+                      const float *psi, float *ux, float *uy, unsigned *status, StepScalars sc,
+                      bool write_populations, cudaStream_t s) {
+  using T = typename S::T;
   dim3 grid((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY);
+  const T *in = static_cast<const T *>(gs);
+  T *out = static_cast<T *>(gout);
   if (write_populations)
-    k_collide<true><<<grid, dim3(BX, BY), 0, s>>>(p, gs, gout, Tdev, psi, ux, uy, status, sc);
+    k_collide<S, true><<<grid, dim3(BX, BY), 0, s>>>(p, in, out, Tdev, psi, ux, uy, status, sc);
   else
-    k_collide<false><<<grid, dim3(BX, BY), 0, s>>>(p, gs, gout, Tdev, psi, ux, uy, status, sc);
+    k_collide<S, false><<<grid, dim3(BX, BY), 0, s>>>(p, in, out, Tdev, psi, ux, uy, status, sc);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_density_psi(const DevParams &p, int storage, const void *gs, const float *Tdev,
+                               float *rho, float *psi, unsigned *status, StepScalars sc,
+                               cudaStream_t s) {
+  switch (storage) {
+    case STORAGE_BF16: return density_psi_t<StoreBF16>(p, gs, Tdev, rho, psi, status, sc, s);
+    case STORAGE_F16: return density_psi_t<StoreF16>(p, gs, Tdev, rho, psi, status, sc, s);
+    default: return density_psi_t<StoreF32>(p, gs, Tdev, rho, psi, status, sc, s);
+  }
+}
+
+cudaError_t launch_collide(const DevParams &p, int storage, const void *gs, void *gout,
+                           const float *Tdev, const float *psi, float *ux, float *uy,
+                           unsigned *status, StepScalars sc, bool write_populations,
+                           cudaStream_t s) {
+  switch (storage) {
+    case STORAGE_BF16:
+      return collide_t<StoreBF16>(p, gs, gout, Tdev, psi, ux, uy, status, sc, write_populations, s);
+    case STORAGE_F16:
+      return collide_t<StoreF16>(p, gs, gout, Tdev, psi, ux, uy, status, sc, write_populations, s);
+    default:
+      return collide_t<StoreF32>(p, gs, gout, Tdev, psi, ux, uy, status, sc, write_populations, s);
+  }
 }
 
 cudaError_t launch_energy(const DevParams &p, const float *Tin, float *Tout, const float *rho,

@@ -45,6 +45,7 @@ class LbmParams(ctypes.Structure):
         ("rho_out", ctypes.c_double),
         ("thermal", ctypes.c_int), ("multiphase", ctypes.c_int),
         ("storage", ctypes.c_int), ("rho_ref", ctypes.c_double), ("kernel", ctypes.c_int),
+        ("p_amp_frac", ctypes.c_double),
     ]
 
 

@@ -103,3 +103,26 @@ def test_womersley_oscillating_channel():
         worst = max(worst, np.abs(ux[:, 0] - ref).max())
         scale = max(scale, np.abs(ref).max())
     assert worst / scale < 1e-2
+
+
+def test_pressure_inlet_imposes_the_eos_pressure():
+    """Section 3.3 inlet: at time t the inlet nodes carry the vapour-branch density
+    whose Peng-Robinson pressure at T_inlet is p0 (1 + a sin(2 pi t / P)), with p0 the
+    pressure of the outlet density."""
+    nx, ny, t = 30, 12, 57
+    p = inputs.base_params(multiphase=0, thermal=0, x_bc=2, p_amp_frac=0.1, u_period=40.0,
+                           rho_out=0.38)
+    o = run(nx, ny, p, np.full((ny, nx), 0.38), t)
+    rho, ux, uy, _ = o.fields()
+    T_in = p["T_inlet"] * o.Tc
+    p0 = oracle.eos_pressure(p, 0.38, T_in)
+    target = p0 * (1 + 0.1 * np.sin(2 * np.pi * t / 40.0))
+    r_in = oracle.inlet_density(p, t)
+    assert oracle.eos_pressure(p, r_in, T_in) == pytest.approx(target, rel=1e-13)
+    # vapour branch: the isotherm still rises there
+    h = 1e-6
+    assert oracle.eos_pressure(p, r_in + h, T_in) > oracle.eos_pressure(p, r_in - h, T_in)
+    assert r_in < 1.0
+    np.testing.assert_allclose(rho[1:-1, 0], r_in, rtol=1e-14)
+    np.testing.assert_allclose(uy[1:-1, 0], 0.0, atol=1e-15)
+    np.testing.assert_allclose(rho[1:-1, -1], 0.38, rtol=1e-14)

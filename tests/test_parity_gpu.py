@@ -88,13 +88,17 @@ CASES = [
     (40, 21, dict(multiphase=0, gx=1e-5, rho_g=0.0)),
     (33, 19, dict(Gw=-1.0, T_wall_left=0.86, T_wall_right=0.78)),
     (33, 19, dict(tau_l=0.8, rho_w=1.0, gy=-1e-5, g_omega=0.01)),
+    # Section 3.3 variant: oscillating pressure inlet, gravity along the channel,
+    # wall temperature falling along x
+    (64, 24, dict(x_bc=2, p_amp_frac=0.1, u_period=60.0, gx=1e-4, T_wall_left=0.86,
+                  T_wall_right=0.70)),
 ]
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("nx,ny,over", CASES)
 def test_small_lattices(nx, ny, over, kernel):
-    p = inputs.base_params(u_amp=0.03, u_period=50.0, **over)
+    p = inputs.base_params(**{"u_amp": 0.03, "u_period": 50.0, **over})
     rho0 = inputs.noisy_density(nx, ny, inputs.RHO_V_086, 0.01, seed=nx * 1000 + ny)
     gpu, ref = run_both(nx, ny, p, rho0, 200, kernel)
     err = rel_errors(gpu, ref)

@@ -1,0 +1,135 @@
+"""Reduced-precision population storage (BF16 / FP16 of f_i/w_i - rho_ref, FP32
+arithmetic, FP64 reductions) against the FP64 oracle.
+
+The stated error bounds (max |X - X_oracle| / max |X_oracle|; velocity as a vector,
+floored at 0.01 like the FP32 parity tests) are the ones the design doc reports; the
+FP32 row is the 1e-5 parity bound for comparison.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_01756_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+STORAGES = {"f32": 0, "bf16": 1, "f16": 2}
+# stated bounds after 1000 updates of the 200 x 50 channel
+# (measured on GB300: f32 9.4e-7 / 6.3e-6 / 2.3e-7, f16 8.0e-4 / 5.3e-3 / 1.5e-4,
+#  bf16 1.6e-2 / 9.0e-2 / 2.4e-3 for rho / u / T)
+CHANNEL_BOUNDS = {
+    "f32": {"rho": 1e-5, "u": 1e-5, "T": 1e-5},
+    "f16": {"rho": 2e-3, "u": 1.5e-2, "T": 5e-4},
+    "bf16": {"rho": 5e-2, "u": 0.25, "T": 1e-2},
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_01756_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def errors(gpu, ref):
+    rho, ux, uy, T = gpu
+    rrho, rux, ruy, rT = ref
+    return {
+        "rho": np.abs(rho - rrho).max() / np.abs(rrho).max(),
+        "u": np.hypot(ux - rux, uy - ruy).max() / max(np.hypot(rux, ruy).max(), 1e-2),
+        "T": np.abs(T - rT).max() / np.abs(rT).max(),
+    }
+
+
+@pytest.fixture(scope="module")
+def channel_reference():
+    w = inputs.workload("channel_200x50")
+    o = oracle.Oracle(w["nx"], w["ny"], w["params"])
+    o.set_fields(inputs.initial_density(w))
+    o.step(1000)
+    return o.fields()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_channel_error_against_oracle(storage, channel_reference):
+    from paper_1803_01756_gb300.lattice import Lattice
+    w = inputs.workload("channel_200x50")
+    lat = Lattice(w["nx"], w["ny"], w["params"], storage=STORAGES[storage])
+    lat.write_fields(inputs.initial_density(w))
+    lat.step(1000)
+    err = errors(lat.read_fields(), channel_reference)
+    lat.close()
+    print(f"\n200x50 channel, 1000 updates, {storage}: " +
+          ", ".join(f"{k} {v:.2e}" for k, v in err.items()))
+    for k, bound in CHANNEL_BOUNDS[storage].items():
+        assert err[k] <= bound, (storage, err)
+
+
+def sessile_drop(nx=80, ny=40):
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    r = np.hypot(x - nx / 2, y + 0.5)
+    return inputs.RHO_V_086 + (inputs.RHO_L_086 - inputs.RHO_V_086) * 0.5 * (1 - np.tanh((r - 14) / 2))
+
+
+def contact_angle(rho):
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_multiphase import contact_angle as ca
+    return ca(rho, 0.5 * (inputs.RHO_V_086 + inputs.RHO_L_086))
+
+
+@pytest.fixture(scope="module")
+def drop_reference():
+    p = inputs.base_params(thermal=0, x_bc=0, y_bc=1, Gw=-1.15)
+    o = oracle.Oracle(80, 40, p)
+    o.set_fields(sessile_drop())
+    o.step(4000)
+    rho = o.fields()[0]
+    return p, rho, contact_angle(rho)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_liquid_drop_density_and_contact_angle(storage, drop_reference):
+    """Sessile drop (density ratio 17): liquid density and contact angle after 4000
+    updates, against the oracle.  Over this many updates the interface amplifies
+    rounding, so even FP32 departs by ~1e-4 in density near the interface (measured
+    8.4e-5) while the contact angle agrees to 0.01 degree; measured f16 2.8e-2 and
+    0.12 degree, bf16 9.2e-2 and 3.8 degrees."""
+    from paper_1803_01756_gb300.lattice import Lattice
+    p, rho_ref, ca_ref = drop_reference
+    lat = Lattice(80, 40, p, storage=STORAGES[storage])
+    lat.write_fields(sessile_drop())
+    lat.step(4000)
+    rho = lat.read_fields()[0]
+    lat.close()
+    err = np.abs(rho - rho_ref).max() / rho_ref.max()
+    ca = contact_angle(rho)
+    print(f"\nsessile drop, {storage}: rho error {err:.2e}, contact angle {ca:.2f} "
+          f"(oracle {ca_ref:.2f})")
+    bound = {"f32": 2e-4, "f16": 8e-2, "bf16": 0.25}[storage]
+    assert err <= bound
+    assert abs(ca - ca_ref) <= {"f32": 0.01, "f16": 0.5, "bf16": 6.0}[storage]
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_16bit_checkpoint_round_trip(storage):
+    from paper_1803_01756_gb300.lattice import Lattice
+    w = inputs.workload("channel_200x50")
+    a = Lattice(w["nx"], w["ny"], w["params"], storage=STORAGES[storage])
+    a.write_fields(inputs.initial_density(w))
+    a.step(40)
+    state = a.read_state()
+    a.step(20)
+    fa = a.read_fields()
+    b = Lattice(w["nx"], w["ny"], w["params"], storage=STORAGES[storage])
+    b.write_state(state)
+    b.step(20)
+    fb = b.read_fields()
+    for x, y in zip(fa, fb):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
