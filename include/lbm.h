@@ -145,6 +145,34 @@ const char *lbm_strerror(int code);
 /* Critical temperature of Eq. 11 for the given parameters. */
 double lbm_critical_temperature(const lbm_params_t *p);
 
+/* ---- batched updates of many lattices (one persistent launch per step) ----
+   A batch groups lattices that share the boundary modes (x_bc class, y_bc), the
+   thermal and multiphase switches and the storage, and that use the fused kernel;
+   sizes and all other parameters may differ.  Each step is one launch whose
+   resident CTAs take tiles of all lattices from one work-list (largest lattices
+   first) through an atomic counter.  The batch borrows the lattices: they stay
+   owned by the caller, must outlive the batch, and while batched should be advanced
+   only through lbm_batch_step (their own t, buffers and status words advance).
+   A lattice's fields after lbm_batch_step equal those after lbm_step alone. */
+typedef struct lbm_batch *lbm_batch_h;
+
+/* LBM_ERR_ARG if a lattice is NULL, repeated, on another device, not on the fused
+   kernel, or differs in modes or storage from the first. */
+int lbm_batch_create(lbm_h *lattices, int n, lbm_batch_h *out);
+/* Advance every lattice of the batch by nsteps updates (enqueued on the stream). */
+int lbm_batch_step(lbm_batch_h b, long nsteps, void *stream);
+/* enable != 0: replay whole chunks of 16 steps from one captured CUDA graph. */
+int lbm_batch_set_graph(lbm_batch_h b, int enable);
+/* Output rows per tile (the work-list granularity; default 64). */
+int lbm_batch_set_tile_rows(lbm_batch_h b, int rows);
+/* Time tile heights 16..128 rows with steps_per_candidate timed updates each (plus two
+   warm-up updates) and keep the fastest.  These are real updates: every lattice
+   advances by 7 * (steps_per_candidate + 2) steps.  Synchronises the stream. */
+int lbm_batch_autotune(lbm_batch_h b, int steps_per_candidate, int *best_rows, void *stream);
+int lbm_batch_info(lbm_batch_h b, int *ntiles, int *grid, int *tile_rows);
+/* Synchronises the device, frees the batch's tables; the lattices are untouched. */
+void lbm_batch_destroy(lbm_batch_h b);
+
 /* Largest nx or ny that lbm_mass_heat_noalloc accepts. */
 #define LBM_NOALLOC_MAX_DIM (1 << 20)
 

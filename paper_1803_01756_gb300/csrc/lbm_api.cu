@@ -9,7 +9,7 @@
 #include <vector>
 
 #include "../../include/lbm.h"
-#include "lbm_internal.h"
+#include "lbm_handle.h"
 
 using lbm::DevParams;
 using lbm::StepScalars;
@@ -27,49 +27,13 @@ struct StateHeader {
   int64_t reserved[4];
 };
 
-enum { KN_DENSITY = 0, KN_COLLIDE, KN_ENERGY, KN_FUSED, KN_COUNT };
+using namespace lbm_host;
 const char *kKernelNames[KN_COUNT] = {"k_density_psi", "k_collide", "k_energy", "k_fused_step"};
 
-struct TimedLaunch {
-  int kind;
-  cudaEvent_t a, b;
-};
 
 }  // namespace
 
-struct lbm_lattice {
-  int device = 0;
-  int nx = 0, ny = 0, pitch = 0;
-  long long plane = 0;
-  lbm_params_t p{};
-  DevParams dp{};
-  double Tc = 0, T_ref = 0, rho_ref = 0;
-  double rho_branch_end = 0;  // vapour-branch end of the isotherm at T_inlet (pressure inlet)
-  long long t = 0;
-  int kernel = LBM_KERNEL_SPLIT;
-  lbm::FusedTiling fused{0, 0};  // CTA tiling of the fused kernel
-  int cur = 0;   // g[cur]: post-collision populations of the previous update
-  int tcur = 0;  // T[tcur]: temperature deviation of time t
-  void *g[2] = {nullptr, nullptr};  // populations, storage-typed elements
-  int esize = 4;                    // bytes per stored population
-  float *T[2] = {nullptr, nullptr};
-  float *rho = nullptr, *psi = nullptr, *ux = nullptr, *uy = nullptr;
-  unsigned *status = nullptr;
-  double *partials = nullptr, *sums = nullptr;
-  int nblocks = 1;
-  double *rho0 = nullptr;  // device staging for lbm_write_fields
-  float *host_stage = nullptr;  // pinned, plane floats
-  double *host_sums = nullptr;  // pinned, 2 doubles
-  size_t device_bytes = 0;
-  // timing
-  bool timing = false;
-  std::vector<TimedLaunch> pending;
-  std::vector<cudaEvent_t> pool;
-  double total_ms[KN_COUNT] = {0, 0, 0, 0};
-  long launches[KN_COUNT] = {0, 0, 0, 0};
-};
-
-namespace {
+namespace lbm_host {
 
 int cuda_fail(cudaError_t e) {
   if (e == cudaSuccess) return LBM_OK;
@@ -77,11 +41,9 @@ int cuda_fail(cudaError_t e) {
   return LBM_ERR_CUDA;
 }
 
-#define LBM_CUDA(expr)                          \
-  do {                                          \
-    cudaError_t _e = (expr);                    \
-    if (_e != cudaSuccess) return cuda_fail(_e); \
-  } while (0)
+}  // namespace lbm_host
+
+namespace {
 
 double critical_temperature(const lbm_params_t &p) {
   return 0.0778 * p.eos_a / (0.45724 * p.eos_b * p.eos_R);
@@ -246,7 +208,9 @@ double inlet_density(const lbm_lattice *h, long long t) {
   return 0.5 * (lo + hi);
 }
 
-StepScalars scalars_at(const lbm_lattice *h, long long t) {
+}  // namespace
+
+lbm::StepScalars lbm_host::scalars_at(const lbm_lattice *h, long long t) {
   StepScalars s;
   double u = h->p.u_period == 0.0 ? h->p.u_amp
                                    : h->p.u_amp * std::sin(2.0 * kPi * (double)t / h->p.u_period);
@@ -255,6 +219,8 @@ StepScalars scalars_at(const lbm_lattice *h, long long t) {
   s.rho_in = h->p.x_bc == LBM_X_PRESSURE_INLET ? (float)inlet_density(h, t) : 0.0f;
   return s;
 }
+
+namespace {
 
 cudaEvent_t take_event(lbm_lattice *h) {
   if (!h->pool.empty()) {

@@ -1,0 +1,294 @@
+// Batched updates of many lattices in one persistent launch per step.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm_handle.h"
+
+using lbm::BatchChannel;
+using lbm::StepScalars;
+
+struct lbm_batch {
+  int device = 0;
+  int storage = 0;
+  lbm::DevParams mode{};  // boundary modes and physics switches shared by all lattices
+  std::vector<lbm_lattice *> lat;  // work-list order: most tiles first
+  int tile_rows = 64;              // output rows per tile (autotuned)
+  int ntiles = 0, grid = 0;
+  BatchChannel *d_ch[2] = {nullptr, nullptr};  // tables for even and odd steps of a call
+  std::vector<BatchChannel> h_ch[2];
+  StepScalars *d_sc = nullptr;                  // [chunk][n] scalars of the next chunk
+  StepScalars *h_sc[2] = {nullptr, nullptr};    // pinned host staging, double buffered
+  cudaEvent_t sc_ev[2] = {nullptr, nullptr};
+  bool sc_used[2] = {false, false};
+  int sc_buf = 0;
+  int *d_counter = nullptr;
+  int chunk = 16;  // steps per scalar upload; also the graph length (even)
+  bool use_graph = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+};
+
+namespace {
+
+using lbm_host::cuda_fail;
+
+int tiles_of(const lbm_lattice *h, int rows) {
+  const int W = lbm::fused_max_width();
+  const int H = std::min(rows, h->ny);
+  return ((h->nx + W - 1) / W) * ((h->ny + H - 1) / H);
+}
+
+void drop_graph(lbm_batch *b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+}
+
+// Work-list layout for the current tile height: lattices with the most work first
+void layout(lbm_batch *b) {
+  std::stable_sort(b->lat.begin(), b->lat.end(), [&](const lbm_lattice *x, const lbm_lattice *y) {
+    return (long long)tiles_of(x, b->tile_rows) * x->nx > (long long)tiles_of(y, b->tile_rows) * y->nx;
+  });
+  b->ntiles = 0;
+  for (auto *h : b->lat) b->ntiles += tiles_of(h, b->tile_rows);
+  drop_graph(b);
+}
+
+// Channel tables for the lattices' current buffers: table 0 for steps at even
+// offsets from now, table 1 for odd offsets.
+int upload_tables(lbm_batch *b, cudaStream_t s) {
+  const int W = lbm::fused_max_width();
+  int begin = 0;
+  for (int par = 0; par < 2; par++) b->h_ch[par].resize(b->lat.size());
+  for (size_t i = 0; i < b->lat.size(); i++) {
+    lbm_lattice *h = b->lat[i];
+    const int H = std::min(b->tile_rows, h->ny);
+    for (int par = 0; par < 2; par++) {
+      const int gc = h->cur ^ par;
+      const int tc = h->dp.thermal ? (h->tcur ^ par) : h->tcur;
+      BatchChannel &c = b->h_ch[par][i];
+      c.p = h->dp;
+      c.gs = h->g[gc];
+      c.gout = h->g[1 - gc];
+      c.Tin = h->T[tc];
+      c.Tout = h->dp.thermal ? h->T[1 - tc] : h->T[tc];
+      c.status = h->status;
+      c.W = W;
+      c.H = H;
+      c.strips = (h->nx + W - 1) / W;
+      c.tile_begin = begin;
+    }
+    begin += tiles_of(h, b->tile_rows);
+  }
+  const size_t bytes = sizeof(BatchChannel) * b->lat.size();
+  for (int par = 0; par < 2; par++)
+    LBM_CUDA(cudaMemcpyAsync(b->d_ch[par], b->h_ch[par].data(), bytes, cudaMemcpyHostToDevice, s));
+  return LBM_OK;
+}
+
+int launch_one(lbm_batch *b, int k, cudaStream_t s) {
+  const int n = (int)b->lat.size();
+  return cuda_fail(lbm::launch_fused_batch(b->mode, b->storage, b->d_ch[k & 1], n,
+                                           b->d_sc + (size_t)k * n, b->ntiles, b->d_counter,
+                                           b->grid, s));
+}
+
+int build_graph(lbm_batch *b) {
+  drop_graph(b);
+  LBM_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = LBM_OK;
+  for (int k = 0; k < b->chunk && rc == LBM_OK; k++) rc = launch_one(b, k, b->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(b->cap_stream, &b->graph);
+  if (rc != LBM_OK) return rc;
+  LBM_CUDA(e);
+  LBM_CUDA(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+  return LBM_OK;
+}
+
+void free_batch(lbm_batch *b) {
+  drop_graph(b);
+  cudaFree(b->d_ch[0]);
+  cudaFree(b->d_ch[1]);
+  cudaFree(b->d_sc);
+  cudaFree(b->d_counter);
+  for (int k = 0; k < 2; k++) {
+    if (b->h_sc[k]) cudaFreeHost(b->h_sc[k]);
+    if (b->sc_ev[k]) cudaEventDestroy(b->sc_ev[k]);
+  }
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(lbm_h *lattices, int n, lbm_batch_h *out) {
+  if (!lattices || n < 1 || !out) return LBM_ERR_ARG;
+  *out = nullptr;
+  lbm_lattice *first = lattices[0];
+  if (!first) return LBM_ERR_ARG;
+  for (int i = 0; i < n; i++) {
+    lbm_lattice *h = lattices[i];
+    if (!h || h->device != first->device || h->kernel != LBM_KERNEL_FUSED) return LBM_ERR_ARG;
+    if (h->dp.y_walls != first->dp.y_walls || h->dp.x_open != first->dp.x_open ||
+        h->dp.thermal != first->dp.thermal || h->dp.multiphase != first->dp.multiphase ||
+        h->p.storage != first->p.storage)
+      return LBM_ERR_ARG;
+    for (int j = 0; j < i; j++)
+      if (lattices[j] == h) return LBM_ERR_ARG;
+  }
+  lbm_batch *b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_ERR_OOM;
+  b->device = first->device;
+  b->storage = first->p.storage;
+  b->mode = first->dp;
+  b->lat.assign(lattices, lattices + n);
+  cudaError_t e = cudaSetDevice(b->device);
+  b->grid = e == cudaSuccess ? lbm::fused_batch_grid(b->mode, b->storage, b->device) : 0;
+  if (b->grid < 1) {
+    delete b;
+    return LBM_ERR_CUDA;
+  }
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMalloc(&b->d_ch[k], sizeof(BatchChannel) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_sc, sizeof(StepScalars) * n * b->chunk);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->d_counter, 0, 2 * sizeof(int));
+  for (int k = 0; k < 2 && e == cudaSuccess; k++)
+    e = cudaMallocHost((void **)&b->h_sc[k], sizeof(StepScalars) * n * b->chunk);
+  for (int k = 0; k < 2 && e == cudaSuccess; k++)
+    e = cudaEventCreateWithFlags(&b->sc_ev[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    delete b;
+    return cuda_fail(e);
+  }
+  layout(b);
+  *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch_h b, long nsteps, void *stream) {
+  if (!b || nsteps < 0) return LBM_ERR_ARG;
+  LBM_CUDA(cudaSetDevice(b->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = upload_tables(b, s);
+  if (rc) return rc;
+  const int n = (int)b->lat.size();
+  long done = 0;
+  int phase = 0;  // parity of the steps taken in this call
+  while (done < nsteps) {
+    const int m = (int)std::min<long>(b->chunk, nsteps - done);
+    const int buf = b->sc_buf;
+    if (b->sc_used[buf]) LBM_CUDA(cudaEventSynchronize(b->sc_ev[buf]));
+    StepScalars *hs = b->h_sc[buf];
+    for (int k = 0; k < m; k++)
+      for (int i = 0; i < n; i++)
+        hs[(size_t)k * n + i] = lbm_host::scalars_at(b->lat[i], b->lat[i]->t + done + k);
+    LBM_CUDA(cudaMemcpyAsync(b->d_sc, hs, sizeof(StepScalars) * n * m, cudaMemcpyHostToDevice, s));
+    LBM_CUDA(cudaEventRecord(b->sc_ev[buf], s));
+    b->sc_used[buf] = true;
+    b->sc_buf ^= 1;
+    if (b->use_graph && m == b->chunk && phase == 0) {
+      if (!b->gexec) {
+        rc = build_graph(b);
+        if (rc) return rc;
+      }
+      LBM_CUDA(cudaGraphLaunch(b->gexec, s));
+    } else {
+      for (int k = 0; k < m; k++) {
+        // k-th step of this chunk runs with the table of its parity in the call
+        const int par = (phase + k) & 1;
+        rc = cuda_fail(lbm::launch_fused_batch(b->mode, b->storage, b->d_ch[par], n,
+                                               b->d_sc + (size_t)k * n, b->ntiles, b->d_counter,
+                                               b->grid, s));
+        if (rc) return rc;
+      }
+    }
+    phase = (phase + m) & 1;
+    done += m;
+  }
+  for (auto *h : b->lat) {
+    h->t += nsteps;
+    if (nsteps & 1) {
+      h->cur ^= 1;
+      if (h->dp.thermal) h->tcur ^= 1;
+    }
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_set_graph(lbm_batch_h b, int enable) {
+  if (!b) return LBM_ERR_ARG;
+  b->use_graph = enable != 0;
+  if (!b->use_graph) drop_graph(b);
+  return LBM_OK;
+}
+
+int lbm_batch_set_tile_rows(lbm_batch_h b, int rows) {
+  if (!b || rows < 1) return LBM_ERR_ARG;
+  b->tile_rows = rows;
+  layout(b);
+  return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch_h b, int steps_per_candidate, int *best_rows, void *stream) {
+  if (!b || steps_per_candidate < 2) return LBM_ERR_ARG;
+  LBM_CUDA(cudaSetDevice(b->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  static const int candidates[] = {16, 24, 32, 48, 64, 96, 128};
+  cudaEvent_t e0, e1;
+  LBM_CUDA(cudaEventCreate(&e0));
+  LBM_CUDA(cudaEventCreate(&e1));
+  const bool graph = b->use_graph;
+  b->use_graph = false;
+  float best = -1.0f;
+  int best_h = b->tile_rows;
+  int rc = LBM_OK;
+  for (int H : candidates) {
+    b->tile_rows = H;
+    layout(b);
+    rc = lbm_batch_step(b, 2, stream);  // warm-up
+    if (rc) break;
+    LBM_CUDA(cudaEventRecord(e0, s));
+    rc = lbm_batch_step(b, steps_per_candidate, stream);
+    if (rc) break;
+    LBM_CUDA(cudaEventRecord(e1, s));
+    LBM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    LBM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (best < 0.0f || ms < best) {
+      best = ms;
+      best_h = H;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->use_graph = graph;
+  b->tile_rows = best_h;
+  layout(b);
+  if (best_rows) *best_rows = best_h;
+  return rc;
+}
+
+int lbm_batch_info(lbm_batch_h b, int *ntiles, int *grid, int *tile_rows) {
+  if (!b) return LBM_ERR_ARG;
+  if (ntiles) *ntiles = b->ntiles;
+  if (grid) *grid = b->grid;
+  if (tile_rows) *tile_rows = b->tile_rows;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch_h b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  free_batch(b);
+  delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// Handle of one lattice (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+namespace lbm_host {
+
+enum { KN_DENSITY = 0, KN_COLLIDE, KN_ENERGY, KN_FUSED, KN_COUNT };
+
+struct TimedLaunch {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+}  // namespace lbm_host
+
+struct lbm_lattice {
+  int device = 0;
+  int nx = 0, ny = 0, pitch = 0;
+  long long plane = 0;
+  lbm_params_t p{};
+  lbm::DevParams dp{};
+  double Tc = 0, T_ref = 0, rho_ref = 0;
+  double rho_branch_end = 0;  // vapour-branch end of the isotherm at T_inlet (pressure inlet)
+  long long t = 0;
+  int kernel = LBM_KERNEL_SPLIT;
+  lbm::FusedTiling fused{0, 0};  // CTA tiling of the fused kernel
+  int cur = 0;   // g[cur]: post-collision populations of the previous update
+  int tcur = 0;  // T[tcur]: temperature deviation of time t
+  void *g[2] = {nullptr, nullptr};  // populations, storage-typed elements
+  int esize = 4;                    // bytes per stored population
+  float *T[2] = {nullptr, nullptr};
+  float *rho = nullptr, *psi = nullptr, *ux = nullptr, *uy = nullptr;
+  unsigned *status = nullptr;
+  double *partials = nullptr, *sums = nullptr;
+  int nblocks = 1;
+  double *rho0 = nullptr;  // device staging for lbm_write_fields
+  float *host_stage = nullptr;  // pinned, plane floats
+  double *host_sums = nullptr;  // pinned, 2 doubles
+  size_t device_bytes = 0;
+  // timing
+  bool timing = false;
+  std::vector<lbm_host::TimedLaunch> pending;
+  std::vector<cudaEvent_t> pool;
+  double total_ms[lbm_host::KN_COUNT] = {0, 0, 0, 0};
+  long launches[lbm_host::KN_COUNT] = {0, 0, 0, 0};
+};
+
+
+namespace lbm_host {
+
+// per-update scalars of time t (inlet velocity or density, body-force phase)
+lbm::StepScalars scalars_at(const lbm_lattice *h, long long t);
+int cuda_fail(cudaError_t e);
+
+}  // namespace lbm_host
+
+#define LBM_CUDA(expr)                                     \
+  do {                                                     \
+    cudaError_t _e = (expr);                               \
+    if (_e != cudaSuccess) return lbm_host::cuda_fail(_e); \
+  } while (0)

@@ -22,6 +22,18 @@ cudaError_t launch_energy(const DevParams &p, const float *Tin, float *Tout, con
                           const float *ux, const float *uy, unsigned *status, StepScalars sc,
                           cudaStream_t s);
 
+// one lattice of a batched fused launch (device-resident table entry)
+struct BatchChannel {
+  DevParams p;
+  const void *gs;  // populations read this step
+  void *gout;      // populations written this step
+  const float *Tin;
+  float *Tout;
+  unsigned *status;
+  int W, H, strips;  // tiling of this lattice
+  int tile_begin;    // index of its first tile in the work-list
+};
+
 // fused path: one launch per update
 struct FusedTiling {
   int W;  // output columns per CTA (at most 118)
@@ -34,6 +46,16 @@ bool fused_supported(const DevParams &p);
 // tiling for one wave of resident CTAs on this device ({0, 0} on failure); also sets
 // the kernel's shared-memory attribute
 FusedTiling fused_tiling(const DevParams &p, int storage, int device);
+
+// batched fused path: a persistent grid of `grid` CTAs walks the tiles of nch
+// lattices (all with the modes of `mode` and storage `storage`); counter: two ints,
+// zero before the first launch, left at zero by every launch
+cudaError_t launch_fused_batch(const DevParams &mode, int storage, const BatchChannel *ch, int nch,
+                               const StepScalars *sc, int ntiles, int *counter, int grid,
+                               cudaStream_t s);
+// resident CTAs of the batched kernel on this device (0 on failure)
+int fused_batch_grid(const DevParams &mode, int storage, int device);
+int fused_max_width();
 
 // set-up and reductions
 cudaError_t launch_init(const DevParams &p, int storage, const double *rho0, void *gout,

@@ -77,6 +77,15 @@ SIGNATURES = {
     "lbm_destroy": ([_vp], None),
     "lbm_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "lbm_critical_temperature": ([ctypes.POINTER(LbmParams)], ctypes.c_double),
+    "lbm_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                          ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "lbm_batch_step": ([_vp, ctypes.c_long, _vp], ctypes.c_int),
+    "lbm_batch_set_graph": ([_vp, ctypes.c_int], ctypes.c_int),
+    "lbm_batch_set_tile_rows": ([_vp, ctypes.c_int], ctypes.c_int),
+    "lbm_batch_autotune": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp], ctypes.c_int),
+    "lbm_batch_info": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                        ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "lbm_batch_destroy": ([_vp], None),
     "lbm_mass_heat_noalloc": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                ctypes.c_double, _vp, _vp], ctypes.c_int),
 }
@@ -254,3 +263,50 @@ class Lattice:
         _check(self._lib.lbm_timing_get(self._h, names, ms, cnt, n, ctypes.byref(count),
                                         _stream_ptr(stream)), "lbm_timing_get")
         return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(count.value, n))}
+
+
+class Batch:
+    """Lattices advanced together, one persistent launch per step (lbm_batch_*).
+
+    The lattices stay owned by the caller and must outlive the batch."""
+
+    def __init__(self, lattices, graph: bool = False, tile_rows: int | None = None):
+        self._lib = load_library()
+        self.lattices = list(lattices)
+        arr = (ctypes.c_void_p * len(self.lattices))(*[l._h.value for l in self.lattices])
+        h = ctypes.c_void_p()
+        _check(self._lib.lbm_batch_create(arr, len(self.lattices), ctypes.byref(h)),
+               "lbm_batch_create")
+        self._h = h
+        if graph:
+            _check(self._lib.lbm_batch_set_graph(self._h, 1), "lbm_batch_set_graph")
+        if tile_rows:
+            _check(self._lib.lbm_batch_set_tile_rows(self._h, int(tile_rows)),
+                   "lbm_batch_set_tile_rows")
+
+    def step(self, nsteps: int = 1, stream=None):
+        _check(self._lib.lbm_batch_step(self._h, int(nsteps), _stream_ptr(stream)),
+               "lbm_batch_step")
+
+    def autotune(self, steps_per_candidate: int = 4, stream=None) -> int:
+        best = ctypes.c_int()
+        _check(self._lib.lbm_batch_autotune(self._h, int(steps_per_candidate), ctypes.byref(best),
+                                            _stream_ptr(stream)), "lbm_batch_autotune")
+        return best.value
+
+    def info(self) -> dict:
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.lbm_batch_info(self._h, ctypes.byref(a), ctypes.byref(b),
+                                        ctypes.byref(c)), "lbm_batch_info")
+        return {"tiles": a.value, "grid": b.value, "tile_rows": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
