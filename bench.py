@@ -303,6 +303,92 @@ def our_arm(args, world, rank, local, dist):
     print(json.dumps(line), flush=True)
 
 
+def serving_jobs(n: int, steps: int, seed: int = 4):
+    """Seeded job stream: 90 % channels with length U[256, 2048], width U[32, 256],
+    wall strength U[-1.25, -1.08] (contact angles ~40-130 degrees), inlet period
+    U[2000, 20000]; 10 % 4096 x 512 channels.  Poisson arrivals at 20 jobs/s."""
+    u = inputs.uniform01(6 * n, seed).reshape(n, 6)
+    jobs, t = [], 0.0
+    for k in range(n):
+        t += -np.log(1.0 - u[k, 5]) / 20.0
+        if u[k, 0] < 0.1:
+            nx, ny = 4096, 512
+        else:
+            nx, ny = int(256 + u[k, 1] * 1792), int(32 + u[k, 2] * 224)
+        p = inputs.base_params(Gw=-1.25 + 0.17 * u[k, 3],
+                               u_period=float(2000 + int(18000 * u[k, 4])))
+        jobs.append(dict(t=t, nx=nx, ny=ny, p=p, steps=steps, seed=1000 + k))
+    return jobs
+
+
+def serving_arm(args):
+    """jobs/hour and latency of the continuous-batching server (BF16 storage) against
+    the same arrivals solved one at a time in FP32 (first come, first served)."""
+    import threading
+    import torch
+    from paper_1803_01756_gb300 import lattice as L
+    torch.cuda.set_device(0)
+    jobs = serving_jobs(args.jobs, args.job_steps)
+    rho0 = [inputs.noisy_density(j["nx"], j["ny"], inputs.RHO_V_086, 0.01, j["seed"]) for j in jobs]
+    free, _ = torch.cuda.mem_get_info()
+    srv = L.Server(hbm_budget=int(0.5 * free), max_active=args.max_active,
+                   chunk_steps=args.chunk_steps)
+    ids = [None] * len(jobs)
+    t0 = time.perf_counter()
+
+    def client():
+        for k, j in enumerate(jobs):
+            delay = t0 + j["t"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids[k] = srv.submit(j["nx"], j["ny"], j["p"], j["steps"], rho0[k], storage=1)
+
+    th = threading.Thread(target=client)
+    th.start()
+    th.join()
+    lat = []
+    for jid in ids:
+        assert srv.wait(jid, 3600) == L.JOB_DONE
+        lat.append(srv.poll(jid)[2])
+    wall = time.perf_counter() - t0
+    peak = srv.stats()["peak_bytes"]
+    srv.close()
+    # sequential FP32 solves of the same stream, one at a time
+    service = []
+    for k, j in enumerate(jobs):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        lt = L.Lattice(j["nx"], j["ny"], j["p"], kernel=L.KERNEL_FUSED)
+        lt.write_fields(rho0[k])
+        lt.step(j["steps"])
+        lt.read_fields()
+        lt.close()
+        service.append(time.perf_counter() - a)
+    finish, seq_lat = 0.0, []
+    for j, sv in zip(jobs, service):
+        start = max(finish, j["t"])
+        finish = start + sv
+        seq_lat.append(finish - j["t"])
+    cells = sum(j["nx"] * j["ny"] * j["steps"] for j in jobs)
+    line = {
+        "metric": "jobs/hour (continuous-batching server)", "value": len(jobs) / wall * 3600,
+        "unit": "jobs/h", "n_gpus": 1, "steps": len(jobs), "warmup": 0,
+        "ms_per_step": wall / len(jobs) * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving: Poisson 20 jobs/s, 90 % 256-2048 x 32-256 channels, "
+                               "10 % 4096x512", "jobs": len(jobs), "steps_per_job": args.job_steps,
+                   "storage": "bf16", "chunk_steps": args.chunk_steps,
+                   "max_active": args.max_active, "peak_device_bytes": peak},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "mlups": cells / wall / 1e6,
+        "sequential_fp32": {"jobs_per_hour": len(jobs) / finish * 3600,
+                            "p50": float(np.percentile(seq_lat, 50)),
+                            "p99": float(np.percentile(seq_lat, 99)),
+                            "mlups": cells / sum(service) / 1e6},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,6 +404,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-inner", type=int, default=100)
     ap.add_argument("--e2e-reps", type=int, default=5)
+    ap.add_argument("--mode", default="lattice", choices=["lattice", "serve"],
+                    help="lattice: MLUPS of one channel; serve: the job server")
+    ap.add_argument("--jobs", type=int, default=160)
+    ap.add_argument("--job-steps", type=int, default=2000)
+    ap.add_argument("--max-active", type=int, default=64)
+    ap.add_argument("--chunk-steps", type=int, default=250)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured")
     args = ap.parse_args()
@@ -326,6 +418,9 @@ def main():
     try:
         if args.impl == "reference":
             reference_arm(args, world, rank)
+        elif args.mode == "serve":
+            if rank == 0:
+                serving_arm(args)
         else:
             our_arm(args, world, rank, local, dist)
     finally:

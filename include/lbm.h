@@ -173,6 +173,52 @@ int lbm_batch_info(lbm_batch_h b, int *ntiles, int *grid, int *tile_rows);
 /* Synchronises the device, frees the batch's tables; the lattices are untouched. */
 void lbm_batch_destroy(lbm_batch_h b);
 
+/* ---- serving: continuous batching of simulation jobs ----
+   A server owns one CUDA stream and one worker thread on `device`.  Jobs (lattice
+   size, parameters, initial density, number of updates) are submitted at any time
+   and queue first come, first served.  The worker admits queued jobs while fewer
+   than max_active run and their device footprint (populations, temperature and
+   scratch of lbm_create) fits in hbm_budget bytes; it then advances all running
+   jobs that share modes together in batched launches (lbm_batch_*), chunk_steps
+   updates per round (fewer when a job has fewer left), reads finished jobs' fields
+   back to host memory and frees their device memory, which admits the next jobs.
+   A job's fields equal those of the same job run alone (lbm_step) within the FP32
+   parity bound. */
+#define LBM_JOB_QUEUED 0
+#define LBM_JOB_RUNNING 1
+#define LBM_JOB_DONE 2  /* other final states are negative LBM_ERR_* codes */
+
+typedef struct lbm_server_config {
+  int device;          /* CUDA device the worker uses */
+  size_t hbm_budget;   /* bytes of device memory all running jobs may hold */
+  int max_active;      /* running jobs at most */
+  long chunk_steps;    /* updates per scheduling round */
+} lbm_server_config_t;
+
+typedef struct lbm_server_stats {
+  long queued, active, completed, failed, rounds;
+  size_t bytes_in_use, peak_bytes;
+} lbm_server_stats_t;
+
+typedef struct lbm_server *lbm_server_h;
+
+int lbm_server_create(const lbm_server_config_t *cfg, lbm_server_h *out);
+/* Queue a job; rho0 ([ny][nx] host doubles, copied) may be NULL for rest at rho_g.
+   Never blocks.  LBM_ERR_BUSY if the job alone exceeds hbm_budget. */
+int lbm_submit(lbm_server_h s, int nx, int ny, const lbm_params_t *p, const double *rho0,
+               long nsteps, long *job_id);
+/* Non-blocking: *state = LBM_JOB_* or a negative error.  When LBM_JOB_DONE, copies the
+   final fields into any non-NULL [ny][nx] host arrays and the submit-to-done time. */
+int lbm_poll(lbm_server_h s, long job_id, int *state, double *rho, double *ux, double *uy,
+             double *T, double *latency_s);
+/* Block until the job leaves the queued and running states or timeout_s passes
+   (LBM_ERR_TIMEOUT). */
+int lbm_wait(lbm_server_h s, long job_id, double timeout_s, int *state);
+int lbm_server_stats(lbm_server_h s, lbm_server_stats_t *st);
+/* Stops the worker after its current round; queued and running jobs are cancelled
+   (state LBM_ERR_ARG). */
+void lbm_server_destroy(lbm_server_h s);
+
 /* Largest nx or ny that lbm_mass_heat_noalloc accepts. */
 #define LBM_NOALLOC_MAX_DIM (1 << 20)
 

@@ -56,6 +56,20 @@ class LbmInfo(ctypes.Structure):
                 ("kernel", ctypes.c_int)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
+                ("max_active", ctypes.c_int), ("chunk_steps", ctypes.c_long)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_long), ("active", ctypes.c_long),
+                ("completed", ctypes.c_long), ("failed", ctypes.c_long),
+                ("rounds", ctypes.c_long), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t)]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE = 0, 1, 2
+
 # every symbol declared in include/lbm.h, with its ctypes signature
 _dp = ctypes.POINTER(ctypes.c_double)
 _vp = ctypes.c_void_p
@@ -86,6 +100,15 @@ SIGNATURES = {
     "lbm_batch_info": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                         ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lbm_batch_destroy": ([_vp], None),
+    "lbm_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)],
+                          ctypes.c_int),
+    "lbm_submit": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(LbmParams), _dp, ctypes.c_long,
+                    ctypes.POINTER(ctypes.c_long)], ctypes.c_int),
+    "lbm_poll": ([_vp, ctypes.c_long, ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp, _dp, _dp],
+                 ctypes.c_int),
+    "lbm_wait": ([_vp, ctypes.c_long, ctypes.c_double, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "lbm_server_stats": ([_vp, ctypes.POINTER(ServerStats)], ctypes.c_int),
+    "lbm_server_destroy": ([_vp], None),
     "lbm_mass_heat_noalloc": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                ctypes.c_double, _vp, _vp], ctypes.c_int),
 }
@@ -303,6 +326,67 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching job server (lbm_server_*): jobs are admitted by device
+    footprint and advanced together in batched launches by a worker thread."""
+
+    def __init__(self, hbm_budget: int, max_active: int = 64, chunk_steps: int = 500,
+                 device: int = 0):
+        self._lib = load_library()
+        cfg = ServerConfig(device, int(hbm_budget), int(max_active), int(chunk_steps))
+        h = ctypes.c_void_p()
+        _check(self._lib.lbm_server_create(ctypes.byref(cfg), ctypes.byref(h)), "lbm_server_create")
+        self._h = h
+        self._shape = {}
+
+    def submit(self, nx: int, ny: int, params: dict, nsteps: int, rho0=None,
+               storage: int = STORAGE_F32, rho_ref: float = 0.0) -> int:
+        p = make_params(params, kernel=KERNEL_FUSED, storage=storage, rho_ref=rho_ref)
+        r = None
+        if rho0 is not None:
+            r = np.ascontiguousarray(rho0, dtype=np.float64).reshape(ny, nx)
+        jid = ctypes.c_long()
+        _check(self._lib.lbm_submit(self._h, int(nx), int(ny), ctypes.byref(p), _dptr(r),
+                                    int(nsteps), ctypes.byref(jid)), "lbm_submit")
+        self._shape[jid.value] = (ny, nx)
+        return jid.value
+
+    def poll(self, job_id: int, fields: bool = False):
+        """(state, fields or None, latency seconds or None); non-blocking."""
+        st = ctypes.c_int()
+        lat = ctypes.c_double(-1.0)
+        arrs = [None] * 4
+        if fields:
+            arrs = [np.empty(self._shape[job_id]) for _ in range(4)]
+        _check(self._lib.lbm_poll(self._h, int(job_id), ctypes.byref(st),
+                                  *[_dptr(a) for a in arrs], ctypes.byref(lat)), "lbm_poll")
+        done = st.value == JOB_DONE
+        return st.value, (tuple(arrs) if (fields and done) else None), (lat.value if done else None)
+
+    def wait(self, job_id: int, timeout_s: float = 600.0) -> int:
+        st = ctypes.c_int()
+        rc = self._lib.lbm_wait(self._h, int(job_id), float(timeout_s), ctypes.byref(st))
+        if rc not in (LBM_OK, -5):
+            _check(rc, "lbm_wait")
+        return st.value if rc == LBM_OK else -5
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self._lib.lbm_server_stats(self._h, ctypes.byref(st)), "lbm_server_stats")
+        return {f[0]: getattr(st, f[0]) for f in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
