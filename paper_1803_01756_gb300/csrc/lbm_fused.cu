@@ -48,13 +48,12 @@ __device__ __forceinline__ int modi(int v, int n) {
 //   grad = 3 sum w_i T(x+e_i) e_i,  lap = 6 sum w_i (T(x+e_i) - T(x)),
 //   K = -u.grad T + cl lap - e1 T - e2 s (1 + kappa - kappa s),  s = sqrt(T/Tc)
 // where cl = lambda/(rho Cv) and e1, e2 carry (dP/dT)_rho T div u / (rho Cv).
-__device__ __forceinline__ float rk_rate(const DevParams &p, const float *__restrict__ Rm,
-                                         const float *__restrict__ R0,
-                                         const float *__restrict__ Rp, int tl, int t, int tr,
-                                         float ux, float uy, float cl, float e1, float e2) {
-  const float c = R0[t];
-  const float v1 = R0[tr], v3 = R0[tl], v2 = Rp[t], v4 = Rm[t];
-  const float v5 = Rp[tr], v6 = Rp[tl], v7 = Rm[tl], v8 = Rm[tr];
+__device__ __forceinline__ float rk_rate(const DevParams &p, const float *__restrict__ R, int im,
+                                         int i0, int ip, float ux, float uy, float cl, float e1,
+                                         float e2) {
+  const float c = R[i0];
+  const float v1 = R[i0 + 1], v3 = R[i0 - 1], v2 = R[ip], v4 = R[im];
+  const float v5 = R[ip + 1], v6 = R[ip - 1], v7 = R[im - 1], v8 = R[im + 1];
   const float gx = (1.0f / 3.0f) * (v1 - v3) + (1.0f / 12.0f) * ((v5 - v7) + (v8 - v6));
   const float gy = (1.0f / 3.0f) * (v2 - v4) + (1.0f / 12.0f) * ((v5 - v7) + (v6 - v8));
   const float lap = (2.0f / 3.0f) * ((v1 + v3) + (v2 + v4) - 4.0f * c) +
@@ -94,7 +93,6 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
   }
   const int xe = min(X0 + W, p.nx);
   const int dxo = c < X0 ? X0 - c : (c >= xe ? c - xe + 1 : 0);  // columns outside the outputs
-  const int tl = t - 1, tr = t + 1;
   // The outlet ghost column copies column nx-1 for u and the RK4 stage fields: the thread
   // of column nx-1 writes those values into the ghost slot too (same thread, no race).
   const bool mirror = XO && c == p.nx - 1;
@@ -114,6 +112,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
   float br_max = 0.0f;      // b rho must stay below the pole of Eq. 11
   float T_min = 1.0f;       // absolute temperature must stay positive
   float fA[9], fB[9];
+  float drhoA = 0.0f, drhoB = 0.0f;  // density deviations of the two newest pulled rows
 #pragma unroll
   for (int i = 0; i < 9; i++) {
     fA[i] = 0.0f;
@@ -125,6 +124,25 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
 #pragma unroll 1
   for (int j = 0; j < J; j++) {
     const int r = Y0 - FHALO + j;
+    // element index of ring row (j - k) at this thread's column, one set per ring period;
+    // shared by every ring and stage (R4(k), R8(k) below)
+    int q4[4], q8[8];
+#pragma unroll
+    for (int d = 0; d < 4; d++) q4[d] = ((j + d) & 3) * FNT + t;
+#pragma unroll
+    for (int d = 0; d < 8; d++) q8[d] = ((j + d) & 7) * FNT + t;
+#define R4(k) q4[(4 - ((k) & 3)) & 3]
+#define R8(k) q8[(8 - ((k) & 7)) & 7]
+    float *const ring_psi = &S.psi[0][0];
+    float2 *const ring_u = &S.u[0][0];
+    float4 *const ring_cf = &S.cf[0][0];
+    float *const ring_T = &S.T[0][0];
+    float *const ring_T2 = &S.T2[0][0];
+    float *const ring_T3 = &S.T3[0][0];
+    float *const ring_T4 = &S.T4[0][0];
+    float4 *const ring_o1 = &S.o1[0][0];
+    float2 *const ring_o2 = &S.o2[0][0];
+    float *const ring_acc = &S.oacc[0][0];
 
     // ---------------- S0 loads: row r ----------------
     const bool s0_row = r < ye + FHALO;
@@ -132,7 +150,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     const int ry = YW ? r : modi(r, p.ny);
     float fc[9];
     unsigned unk = 0u;
-    float Tc = 0.0f;
+    float Tc = 0.0f, drhoC = 0.0f;
     if (s0_row && !r_solid) {
       const int own = ry * p.pitch + cx;
       if (col_interior && ry > 0 && ry < p.ny - 1) {
@@ -149,32 +167,32 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     {
       const int q = r - 2;
       if (j >= 3 && q < ye + 4 && dxo <= 4) {
-        const int sl = (j - 2) & 3;
+        const int sl = R4(2);
         const bool solid = YW && (q < 0 || q >= p.ny);
         if (solid) {
-          S.u[sl][t] = make_float2(0.0f, 0.0f);
+          if (TH) ring_u[sl] = make_float2(0.0f, 0.0f);
         } else if (col_in) {
-          if (!p.p_inlet) S.u[sl][t] = make_float2(sc.u_in, 0.0f);
+          if (TH && !p.p_inlet) ring_u[sl] = make_float2(sc.u_in, 0.0f);
         } else if (!col_out) {
           const int qy = YW ? q : modi(q, p.ny);
-          const float drho = sum9(fB);
+          const float drho = drhoB;
           const float rho = p.rho_ref + drho;
           Force F{0.0f, 0.0f, 0.0f};
           if (MP) {
-            const int pm = (j - 3) & 3, p0 = (j - 2) & 3, pp = (j - 1) & 3;
+            const int pm = R4(3), p0 = R4(2), pp = R4(1);
             const bool sdn = YW && q - 1 < 0;
             const bool sup = YW && q + 1 >= p.ny;
             float dn[9];
             dn[0] = 0.0f;
-            dn[1] = S.psi[p0][t + 1];
-            dn[2] = S.psi[pp][t];
-            dn[3] = S.psi[p0][t - 1];
-            dn[4] = S.psi[pm][t];
-            dn[5] = S.psi[pp][t + 1];
-            dn[6] = S.psi[pp][t - 1];
-            dn[7] = S.psi[pm][t - 1];
-            dn[8] = S.psi[pm][t + 1];
-            const float dpc = S.psi[p0][t];
+            dn[1] = ring_psi[p0 + 1];
+            dn[2] = ring_psi[pp];
+            dn[3] = ring_psi[p0 - 1];
+            dn[4] = ring_psi[pm];
+            dn[5] = ring_psi[pp + 1];
+            dn[6] = ring_psi[pp - 1];
+            dn[7] = ring_psi[pm - 1];
+            dn[8] = ring_psi[pm + 1];
+            const float dpc = ring_psi[p0];
             if (!sdn && !sup) {
               // no wall neighbour: F = -G psi sum w dpsi e  (Eq. 9; sum w e = 0)
               const float qx = (1.0f / 3.0f) * (dn[1] - dn[3]) +
@@ -192,7 +210,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
               float psiw = 0.0f;
               if (p.rho_w > 0.0f) {
                 unsigned st_unused = 0;
-                psiw = pseudopotential(p, p.rho_w, p.T_ref + S.T[(j - 2) & 7][t], st_unused);
+                psiw = pseudopotential(p, p.rho_w, p.T_ref + ring_T[R8(2)], st_unused);
               }
               F = interaction_force(p, dpc, dn, solid_mask, psiw);
             }
@@ -218,12 +236,14 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             ux = (jx + 0.5f * F.Fx) * inv_rho;
             uy = (jy + 0.5f * F.Fy) * inv_rho;
           }
-          S.u[sl][t] = make_float2(ux, uy);
-          if (mirror) S.u[sl][t + 1] = make_float2(ux, uy);
-          if (mirror_in) S.u[sl][t - 1] = make_float2(ux, uy);
-          const float br = p.eos_b * rho;
-          S.cf[sl][t] = make_float4(p.lam_cv * inv_rho, p.R_cv / (1.0f - br),
-                                    p.akap_cv * rho / (1.0f + 2.0f * br - br * br), 0.0f);
+          if (TH) {
+            ring_u[sl] = make_float2(ux, uy);
+            if (mirror) ring_u[sl + 1] = make_float2(ux, uy);
+            if (mirror_in) ring_u[sl - 1] = make_float2(ux, uy);
+            const float br = p.eos_b * rho;
+            ring_cf[sl] = make_float4(p.lam_cv * inv_rho, p.R_cv / (1.0f - br),
+                                      p.akap_cv * rho / (1.0f + 2.0f * br - br * br), 0.0f);
+          }
         }
       }
     }
@@ -233,32 +253,32 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       {
         const int q = r - 4;
         if (j >= 6 && q < ye + 3 && dxo <= 3) {
-          const int sl = (j - 4) & 3;
+          const int sl = R4(4);
           const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
-            S.T2[sl][t] = twall;
+            ring_T2[sl] = twall;
           } else if (col_in) {
-            S.T2[sl][t] = p.T_inlet_dev;
+            ring_T2[sl] = p.T_inlet_dev;
           } else if (!col_out) {
-            const int um = (j - 5) & 3, u0 = (j - 4) & 3, up = (j - 3) & 3;
-            const float2 a1 = S.u[u0][tr], a3 = S.u[u0][tl], a2 = S.u[up][t], a4 = S.u[um][t];
-            const float2 a5 = S.u[up][tr], a6 = S.u[up][tl], a7 = S.u[um][tl], a8 = S.u[um][tr];
+            const int um = R4(5), u0 = R4(4), up = R4(3);
+            const float2 a1 = ring_u[u0 + 1], a3 = ring_u[u0 - 1], a2 = ring_u[up], a4 = ring_u[um];
+            const float2 a5 = ring_u[up + 1], a6 = ring_u[up - 1], a7 = ring_u[um - 1],
+                         a8 = ring_u[um + 1];
             // div u = 3 sum w_i u(x+e_i).e_i
             const float divu = (1.0f / 3.0f) * ((a1.x - a3.x) + (a2.y - a4.y)) +
                                (1.0f / 12.0f) * ((a5.x + a5.y) - (a6.x - a6.y) -
                                                  (a7.x + a7.y) + (a8.x - a8.y));
-            const float2 uo = S.u[u0][t];
-            const float4 cf = S.cf[u0][t];
+            const float2 uo = ring_u[u0];
+            const float4 cf = ring_cf[u0];
             const float e1 = cf.y * divu, e2 = cf.z * divu;
-            const float Tb = S.T[(j - 4) & 7][t];
-            const float h1 = rk_rate(p, S.T[(j - 5) & 7], S.T[(j - 4) & 7], S.T[(j - 3) & 7], tl,
-                                     t, tr, uo.x, uo.y, cf.x, e1, e2);
-            S.T2[sl][t] = Tb + 0.5f * h1;
-            if (mirror) S.T2[sl][t + 1] = Tb + 0.5f * h1;
-            const int o = (j - 4) & 7;
-            S.o1[o][t] = make_float4(uo.x, uo.y, cf.x, e1);
-            S.o2[o][t] = make_float2(e2, Tb);
-            S.oacc[o][t] = h1;
+            const int t0 = R8(4);
+            const float Tb = ring_T[t0];
+            const float h1 = rk_rate(p, ring_T, R8(5), t0, R8(3), uo.x, uo.y, cf.x, e1, e2);
+            ring_T2[sl] = Tb + 0.5f * h1;
+            if (mirror) ring_T2[sl + 1] = Tb + 0.5f * h1;
+            ring_o1[t0] = make_float4(uo.x, uo.y, cf.x, e1);
+            ring_o2[t0] = make_float2(e2, Tb);
+            ring_acc[t0] = h1;
           }
         }
       }
@@ -266,21 +286,20 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       {
         const int q = r - 6;
         if (j >= 9 && q < ye + 2 && dxo <= 2) {
-          const int sl = (j - 6) & 3;
+          const int sl = R4(6);
           const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
-            S.T3[sl][t] = twall;
+            ring_T3[sl] = twall;
           } else if (col_in) {
-            S.T3[sl][t] = p.T_inlet_dev;
+            ring_T3[sl] = p.T_inlet_dev;
           } else if (!col_out) {
-            const int o = (j - 6) & 7;
-            const float4 w1 = S.o1[o][t];
-            const float2 w2 = S.o2[o][t];
-            const float h2 = rk_rate(p, S.T2[(j - 7) & 3], S.T2[(j - 6) & 3], S.T2[(j - 5) & 3], tl,
-                                     t, tr, w1.x, w1.y, w1.z, w1.w, w2.x);
-            S.T3[sl][t] = w2.y + 0.5f * h2;
-            if (mirror) S.T3[sl][t + 1] = w2.y + 0.5f * h2;
-            S.oacc[o][t] += 2.0f * h2;
+            const int o = R8(6);
+            const float4 w1 = ring_o1[o];
+            const float2 w2 = ring_o2[o];
+            const float h2 = rk_rate(p, ring_T2, R4(7), sl, R4(5), w1.x, w1.y, w1.z, w1.w, w2.x);
+            ring_T3[sl] = w2.y + 0.5f * h2;
+            if (mirror) ring_T3[sl + 1] = w2.y + 0.5f * h2;
+            ring_acc[o] += 2.0f * h2;
           }
         }
       }
@@ -288,21 +307,20 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       {
         const int q = r - 8;
         if (j >= 12 && q < ye + 1 && dxo <= 1) {
-          const int sl = (j - 8) & 3;
+          const int sl = R4(8);
           const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
-            S.T4[sl][t] = twall;
+            ring_T4[sl] = twall;
           } else if (col_in) {
-            S.T4[sl][t] = p.T_inlet_dev;
+            ring_T4[sl] = p.T_inlet_dev;
           } else if (!col_out) {
-            const int o = (j - 8) & 7;
-            const float4 w1 = S.o1[o][t];
-            const float2 w2 = S.o2[o][t];
-            const float h3 = rk_rate(p, S.T3[(j - 9) & 3], S.T3[(j - 8) & 3], S.T3[(j - 7) & 3], tl,
-                                     t, tr, w1.x, w1.y, w1.z, w1.w, w2.x);
-            S.T4[sl][t] = w2.y + h3;
-            if (mirror) S.T4[sl][t + 1] = w2.y + h3;
-            S.oacc[o][t] += 2.0f * h3;
+            const int o = R8(8);
+            const float4 w1 = ring_o1[o];
+            const float2 w2 = ring_o2[o];
+            const float h3 = rk_rate(p, ring_T3, R4(9), sl, R4(7), w1.x, w1.y, w1.z, w1.w, w2.x);
+            ring_T4[sl] = w2.y + h3;
+            if (mirror) ring_T4[sl + 1] = w2.y + h3;
+            ring_acc[o] += 2.0f * h3;
           }
         }
       }
@@ -310,12 +328,12 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       {
         const int q = r - 10;
         if (j >= 15 && q < ye && dxo == 0) {
-          const int o = (j - 10) & 7;
-          const float4 w1 = S.o1[o][t];
-          const float2 w2 = S.o2[o][t];
-          const float h4 = rk_rate(p, S.T4[(j - 11) & 3], S.T4[(j - 10) & 3], S.T4[(j - 9) & 3],
-                                   tl, t, tr, w1.x, w1.y, w1.z, w1.w, w2.x);
-          const float Tn = w2.y + (S.oacc[o][t] + h4) * (1.0f / 6.0f);
+          const int o = R8(10);
+          const float4 w1 = ring_o1[o];
+          const float2 w2 = ring_o2[o];
+          const float h4 = rk_rate(p, ring_T4, R4(11), R4(10), R4(9), w1.x, w1.y, w1.z, w1.w,
+                                   w2.x);
+          const float Tn = w2.y + (ring_acc[o] + h4) * (1.0f / 6.0f);
           chk += Tn;
           T_min = fminf(T_min, p.T_ref + Tn);
           Tout[q * p.pitch + c] = Tn;
@@ -325,17 +343,18 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
 
     // ---------------- S0 finish: row r ----------------
     if (s0_row) {
-      const int sl = j & 3, sT = j & 7;
+      const int sl = R4(0), sT = R8(0);
       if (r_solid) {
-        S.T[sT][t] = twall;
-        S.psi[sl][t] = 0.0f;
+        ring_T[sT] = twall;
+        ring_psi[sl] = 0.0f;
       } else {
         pull_fix(p, cx, sc, fc, unk);
-        S.T[sT][t] = col_in ? p.T_inlet_dev : Tc;
+        ring_T[sT] = col_in ? p.T_inlet_dev : Tc;
         float dpsi = 0.0f;
         const float drho = sum9(fc);
+        drhoC = drho;
         if (MP) dpsi = pseudopotential_dev(p, drho, Tc, st);
-        S.psi[sl][t] = dpsi;
+        ring_psi[sl] = dpsi;
         if (!col_in && !col_out) {
           const float rho = p.rho_ref + drho;
           rho_min = fminf(rho_min, rho);
@@ -350,6 +369,10 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       fB[i] = fA[i];
       fA[i] = fc[i];
     }
+    drhoB = drhoA;
+    drhoA = drhoC;
+#undef R4
+#undef R8
     __syncthreads();
   }
   if (!isfinite(chk)) st |= ST_NAN;
