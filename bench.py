@@ -37,6 +37,10 @@ BYTES_PER_CELL_UPDATE = 80
 SPLIT_KERNEL_BYTES = {"k_density_psi": 36 + 4 + 8, "k_collide": 36 + 4 + 36 + 8,
                       "k_energy": 4 + 4 + 8 + 4, "k_fused_step": 80}
 L2_BYTES = 129e6
+# DRAM bytes (read + write) of one k_fused_step launch on the 4096 x 512 channel with
+# FP32 storage, from ncu (profiles/k_fused_step_channel_4096x512.md); reported only
+# for that kernel, workload and storage.  Re-measure whenever the kernel changes.
+FUSED_F32_4096x512_DRAM_BYTES = 109.558272e6 + 40.466688e6
 
 
 def env_int(name, default):
@@ -241,11 +245,15 @@ def our_arm(args, world, rank, local, dist):
     top = max(per_kernel.items(), key=lambda kv: kv[1][0])
     top_name, (top_ms, top_n) = top
     per_cell = bytes_cell if top_name == "k_fused_step" else SPLIT_KERNEL_BYTES[top_name]
+    traffic = args.traffic
+    if (traffic is None and top_name == "k_fused_step" and args.storage == "f32"
+            and args.workload == "channel_4096x512"):
+        traffic = FUSED_F32_4096x512_DRAM_BYTES
     bytes_per_launch = per_cell * cells
     achieved = bytes_per_launch / (top_ms / top_n / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": args.traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+                "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": top_ms / top_n * 1e3,
                 "kernel_share": {k: v[0] / sum(x[0] for x in per_kernel.values())
                                  for k, v in per_kernel.items()}}
@@ -392,7 +400,7 @@ def serving_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="channel_4096x512", choices=sorted(inputs.WORKLOADS))
