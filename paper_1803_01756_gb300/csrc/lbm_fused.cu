@@ -23,7 +23,10 @@ namespace lbm {
 
 namespace {
 
-constexpr int FNT = 128;             // threads per CTA, one lattice column each
+#ifndef LBM_FUSED_THREADS
+#define LBM_FUSED_THREADS 128
+#endif
+constexpr int FNT = LBM_FUSED_THREADS;  // threads per CTA, one lattice column each
 constexpr int FHALO = 5;             // psi is needed 5 nodes beyond the outputs
 constexpr int FW = FNT - 2 * FHALO;  // output columns per CTA
 
@@ -93,17 +96,35 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
   }
   const int xe = min(X0 + W, p.nx);
   const int dxo = c < X0 ? X0 - c : (c >= xe ? c - xe + 1 : 0);  // columns outside the outputs
-  // The outlet ghost column copies column nx-1 for u and the RK4 stage fields: the thread
-  // of column nx-1 writes those values into the ghost slot too (same thread, no race).
-  const bool mirror = XO && c == p.nx - 1;
-  // with a pressure inlet the inlet ghost copies the velocity of column 0 the same way
-  const bool mirror_in = XO && p.p_inlet && c == 0;
+  // Ghost columns beyond an open end hold copies that the thread of the adjacent
+  // boundary column writes into their ring slots (same thread, no race): the outlet
+  // ghost copies column nx-1 (psi, T, u and the RK4 stage fields), the inlet ghost
+  // copies psi of column 0 (zero gradient) and holds T_inlet, and with a pressure inlet
+  // also copies the velocity of column 0.  Only the ghost column next to the domain is
+  // read by a needed stencil, so the other ghost threads do no work in S0.
+  const bool ghost = col_in || col_out;
+  const bool mirror = XO && c == p.nx - 1 && t + 1 < FNT;
+  const bool mirror_in0 = XO && c == 0 && t >= 1;
+  const bool mirror_in = mirror_in0 && p.p_inlet;
   const float twall = wall_T_dev(p, cx);
 
-  // pull offsets of an interior node relative to its own index (Eq. 12, f_i(x) = f*_i(x - e_i))
+  // Pull offsets relative to the node's own index (Eq. 12, f_i(x) = f*_i(x - e_i)), used
+  // on every row not next to a wall.  Next to a periodic seam the source column wraps;
+  // at an open end the populations entering from outside (Zou-He unknowns) read any
+  // in-bounds element of their plane and are replaced by pull_fix.
   int poff[9];
+  unsigned unk_edge = 0u;
 #pragma unroll
-  for (int i = 0; i < 9; i++) poff[i] = i * (int)p.plane - ey(i) * p.pitch - ex(i);
+  for (int i = 0; i < 9; i++) {
+    poff[i] = i * (int)p.plane - ey(i) * p.pitch - ex(i);
+    if (!XO) {
+      if (cx == 0 && ex(i) == 1) poff[i] += p.nx;
+      if (cx == p.nx - 1 && ex(i) == -1) poff[i] -= p.nx;
+    } else {
+      if (cx == 0 && ex(i) == 1) unk_edge |= 1u << i;
+      if (cx == p.nx - 1 && ex(i) == -1) unk_edge |= 1u << i;
+    }
+  }
 
   unsigned st = 0;
   // running checks folded into status bits once at the end
@@ -118,7 +139,6 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     fA[i] = 0.0f;
     fB[i] = 0.0f;
   }
-  const bool col_interior = cx > 0 && cx < p.nx - 1;
 
   const int J = (ye - Y0) + 3 * FHALO;
 #pragma unroll 1
@@ -151,12 +171,13 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     float fc[9];
     unsigned unk = 0u;
     float Tc = 0.0f, drhoC = 0.0f;
-    if (s0_row && !r_solid) {
+    if (s0_row && !r_solid && !ghost) {
       const int own = ry * p.pitch + cx;
-      if (col_interior && ry > 0 && ry < p.ny - 1) {
+      if (ry > 0 && ry < p.ny - 1) {
         const typename ST::T *src = gs + own;
 #pragma unroll
         for (int i = 0; i < 9; i++) fc[i] = ST::load(src + poff[i], i);
+        unk = unk_edge;
       } else {
         pull_load<ST>(p, gs, cx, ry, fc, unk);
       }
@@ -347,21 +368,27 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       if (r_solid) {
         ring_T[sT] = twall;
         ring_psi[sl] = 0.0f;
-      } else {
+      } else if (!ghost) {
         pull_fix(p, cx, sc, fc, unk);
-        ring_T[sT] = col_in ? p.T_inlet_dev : Tc;
+        ring_T[sT] = Tc;
         float dpsi = 0.0f;
         const float drho = sum9(fc);
         drhoC = drho;
         if (MP) dpsi = pseudopotential_dev(p, drho, Tc, st);
         ring_psi[sl] = dpsi;
-        if (!col_in && !col_out) {
-          const float rho = p.rho_ref + drho;
-          rho_min = fminf(rho_min, rho);
-          br_max = fmaxf(br_max, p.eos_b * rho);
-          T_min = fminf(T_min, p.T_ref + Tc);
-          chk += rho;
+        if (mirror) {
+          ring_T[sT + 1] = Tc;
+          ring_psi[sl + 1] = dpsi;
         }
+        if (mirror_in0) {
+          ring_T[sT - 1] = p.T_inlet_dev;
+          ring_psi[sl - 1] = dpsi;
+        }
+        const float rho = p.rho_ref + drho;
+        rho_min = fminf(rho_min, rho);
+        br_max = fmaxf(br_max, p.eos_b * rho);
+        T_min = fminf(T_min, p.T_ref + Tc);
+        chk += rho;
       }
     }
 #pragma unroll
@@ -383,7 +410,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
 }
 
 template <bool YW, bool XO, bool TH, bool MP, class ST>
-__global__ void __launch_bounds__(FNT, 4)
+__global__ void __launch_bounds__(FNT, 512 / FNT)
     k_fused_step(DevParams p, const typename ST::T *__restrict__ gs,
                  typename ST::T *__restrict__ gout, const float *__restrict__ Tin,
                  float *__restrict__ Tout, unsigned *status, StepScalars sc, int H, int W) {
@@ -397,7 +424,7 @@ __global__ void __launch_bounds__(FNT, 4)
 // work-list through an atomic counter (largest lattices first), so uneven lattice
 // sizes balance across the SMs.  The last CTA to leave resets the counters.
 template <bool YW, bool XO, bool TH, bool MP, class ST>
-__global__ void __launch_bounds__(FNT, 4)
+__global__ void __launch_bounds__(FNT, 512 / FNT)
     k_fused_batch(const BatchChannel *__restrict__ ch, int nch, const StepScalars *__restrict__ sc,
                   int ntiles, int *counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

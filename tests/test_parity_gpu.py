@@ -92,6 +92,11 @@ CASES = [
     # wall temperature falling along x
     (64, 24, dict(x_bc=2, p_amp_frac=0.1, u_period=60.0, gx=1e-4, T_wall_left=0.86,
                   T_wall_right=0.70)),
+    # wide enough for strips with no boundary column (the fused kernel's steady part)
+    (400, 40, dict()),
+    (400, 38, dict(y_bc=0, x_bc=0)),
+    (390, 36, dict(x_bc=2, p_amp_frac=0.1, u_period=60.0, gx=1e-4)),
+    (380, 34, dict(thermal=0, x_bc=0)),
 ]
 
 
@@ -126,6 +131,20 @@ def test_droplet_with_liquid(kernel):
     r = np.hypot(x - nx / 2, y + 0.5)
     rho0 = inputs.RHO_V_086 + (inputs.RHO_L_086 - inputs.RHO_V_086) * 0.5 * (1 - np.tanh((r - 10) / 2))
     gpu, ref = run_both(nx, ny, p, rho0, 300, kernel)
+    err = rel_errors(gpu, ref)
+    assert max(err.values()) <= TOL, err
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_wide_channel_with_liquid(kernel):
+    """Liquid columns across a channel wide enough for boundary-free strips, so that
+    the whole EOS range passes through the fused kernel's steady part."""
+    nx, ny = 420, 40
+    p = inputs.base_params(u_amp=0.02, u_period=400.0)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    r = np.minimum(np.hypot(x - 150, y - 12), np.hypot(x - 290, y - 27))
+    rho0 = inputs.RHO_V_086 + (inputs.RHO_L_086 - inputs.RHO_V_086) * 0.5 * (1 - np.tanh((r - 8) / 2))
+    gpu, ref = run_both(nx, ny, p, rho0, 100, kernel)
     err = rel_errors(gpu, ref)
     assert max(err.values()) <= TOL, err
 
