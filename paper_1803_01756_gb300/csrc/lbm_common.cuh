@@ -155,14 +155,14 @@ __device__ __forceinline__ float pseudopotential_dev(const DevParams &p, float d
   const float rho = p.rho_ref + drho;
   const float T = p.T_ref + dT;
   const float br = p.eos_b * rho;
-  const float inv1 = 1.0f / (1.0f - br);
-  const float invD = 1.0f / (1.0f + 2.0f * br - br * br);
+  const float inv1 = __fdividef(1.0f, 1.0f - br);
+  const float invD = __fdividef(1.0f, 1.0f + 2.0f * br - br * br);
   const float A = rho * inv1;
   const float B = rho * rho * invD;
   const float dA = drho * inv1 * p.inv_1mbr;
   const float dB = drho * (rho + p.rho_ref + 2.0f * br * p.rho_ref) * invD * p.inv_Dr;
   const float s = sqrtf(T * p.inv_Tc);
-  const float ds = dT * p.inv_Tc / (s + p.sr);
+  const float ds = __fdividef(dT * p.inv_Tc, s + p.sr);
   const float r = 1.0f + p.kappa * (1.0f - s);
   const float dphi = -p.kappa * ds * (r + p.rphi_r);
   const float dP = p.eos_R * (dT * A + p.T_ref * dA) - p.eos_a * (dphi * B + p.phi_r * dB);
@@ -173,7 +173,7 @@ __device__ __forceinline__ float pseudopotential_dev(const DevParams &p, float d
     return -p.psi_r;  // psi = 0
   }
   const float den = sqrtf(psi2) + p.psi_r;
-  return den > 0.0f ? dpsi2 / den : 0.0f;
+  return den > 0.0f ? __fdividef(dpsi2, den) : 0.0f;
 }
 
 // ---------------------------------------------------------------------------
@@ -320,16 +320,16 @@ __device__ __forceinline__ Force interaction_force(const DevParams &p, float dps
 
 // ---------------------------------------------------------------------------
 // Moment-space collision of Eq. 7 with Li's forcing (Eq. 8), written in closed
-// form on the deviation populations.  In: pulled g, total force F, fm2 =
-// |sum w psi e|^2.  Out: post-collision deviations gs.  Returns rho and u.
+// form on the deviation populations.  In: pulled g, their sum drho = sum9(g),
+// total force F, fm2 = |sum w psi e|^2.  Out: post-collision deviations gs.
+// Returns rho and u.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void collide(const DevParams &p, const float g[9], float Fx, float Fy,
-                                        float fm2, float gs[9], float &rho_out, float &ux_out,
-                                        float &uy_out) {
+__device__ __forceinline__ void collide(const DevParams &p, const float g[9], float drho, float Fx,
+                                        float Fy, float fm2, float gs[9], float &rho_out,
+                                        float &ux_out, float &uy_out) {
   // n = M g (Eq. 6 on deviations; m = n + rho_ref (1, -2, 1, 0, ...))
   const float sa = g[1] + g[2] + g[3] + g[4];
   const float sd = g[5] + g[6] + g[7] + g[8];
-  const float drho = g[0] + sa + sd;
   const float n1 = -4.0f * g[0] - sa + 2.0f * sd;
   const float n2 = 4.0f * g[0] - 2.0f * sa + sd;
   const float d57 = g[5] - g[7], d68 = g[6] - g[8];
@@ -341,7 +341,7 @@ __device__ __forceinline__ void collide(const DevParams &p, const float g[9], fl
   const float n8 = g[5] - g[6] + g[7] - g[8];
 
   const float rho = p.rho_ref + drho;
-  const float inv_rho = 1.0f / rho;
+  const float inv_rho = __fdividef(1.0f, rho);
   const float ux = (jx + 0.5f * Fx) * inv_rho;  // Eq. 13
   const float uy = (jy + 0.5f * Fy) * inv_rho;
   const float jxe = rho * ux, jye = rho * uy;
@@ -353,7 +353,7 @@ __device__ __forceinline__ void collide(const DevParams &p, const float g[9], fl
     s_nu = p.s_nu_const;
   } else {
     float fr = fminf(fmaxf((rho - p.rho_g) * p.inv_drho, 0.0f), 1.0f);
-    s_nu = 1.0f / (p.tau_g + fr * p.dtau);  // Eq. 5
+    s_nu = __fdividef(1.0f, p.tau_g + fr * p.dtau);  // Eq. 5
   }
 
   // m* - rho_ref c, moment by moment (Eq. 7) with (1 - s/2) S from Eq. 8, each already

@@ -27,6 +27,9 @@ namespace {
 #define LBM_FUSED_THREADS 128
 #endif
 constexpr int FNT = LBM_FUSED_THREADS;  // threads per CTA, one lattice column each
+#ifndef LBM_FUSED_MIN_CTAS
+#define LBM_FUSED_MIN_CTAS (512 / LBM_FUSED_THREADS)
+#endif
 constexpr int FHALO = 5;             // psi is needed 5 nodes beyond the outputs
 constexpr int FW = FNT - 2 * FHALO;  // output columns per CTA
 
@@ -67,8 +70,8 @@ __device__ __forceinline__ float rk_rate(const DevParams &p, const float *__rest
   return -(ux * gx + uy * gy) + cl * lap - e1 * Tabs - e2 * s * (1.0f + p.kappa - p.kappa * s);
 }
 
-// One tile of the fused update: output columns [bx W, bx W + W) and rows
-// [by H, by H + H) of one lattice.  Boundary modes and physics switches are
+// One tile of the fused update: output columns [X0, X0 + W) and rows [Y0, ye) of
+// one lattice.  Boundary modes and physics switches are
 // compile-time parameters: YW walls in y, XO open ends in x, TH energy equation,
 // MP pseudopotential forces; ST the population storage.
 template <bool YW, bool XO, bool TH, bool MP, class ST>
@@ -76,12 +79,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
                                            typename ST::T *__restrict__ gout,
                                            const float *__restrict__ Tin,
                                            float *__restrict__ Tout, unsigned *status,
-                                           const StepScalars &sc, int bx, int by, int H, int W,
+                                           const StepScalars &sc, int X0, int W, int Y0, int ye,
                                            FusedSmem &S) {
   const int t = threadIdx.x;
-  const int X0 = bx * W;
-  const int Y0 = by * H;
-  const int ye = min(Y0 + H, p.ny);
   const int c = X0 - FHALO + t;  // lattice column of this thread
 
   // column kind: domain (wrapped when periodic) or a ghost beyond an open end
@@ -140,17 +140,19 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     fB[i] = 0.0f;
   }
 
+  // element index of ring row (j - k) at this thread's column, shared by every ring and
+  // stage (R4(k), R8(k) below): q4[d] = ((j + d) & 3) FNT + t, q8[d] = ((j + d) & 7) FNT + t,
+  // rotated by one position per row step
+  int q4[4], q8[8];
+#pragma unroll
+  for (int d = 0; d < 4; d++) q4[d] = d * FNT + t;
+#pragma unroll
+  for (int d = 0; d < 8; d++) q8[d] = d * FNT + t;
+
   const int J = (ye - Y0) + 3 * FHALO;
 #pragma unroll 1
   for (int j = 0; j < J; j++) {
     const int r = Y0 - FHALO + j;
-    // element index of ring row (j - k) at this thread's column, one set per ring period;
-    // shared by every ring and stage (R4(k), R8(k) below)
-    int q4[4], q8[8];
-#pragma unroll
-    for (int d = 0; d < 4; d++) q4[d] = ((j + d) & 3) * FNT + t;
-#pragma unroll
-    for (int d = 0; d < 8; d++) q8[d] = ((j + d) & 7) * FNT + t;
 #define R4(k) q4[(4 - ((k) & 3)) & 3]
 #define R8(k) q8[(8 - ((k) & 7)) & 7]
     float *const ring_psi = &S.psi[0][0];
@@ -244,14 +246,14 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           float ux, uy, inv_rho;
           if (dxo == 0 && q >= Y0 && q < ye) {
             float gn[9], rr;
-            collide(p, fB, F.Fx, F.Fy, F.fm2, gn, rr, ux, uy);
+            collide(p, fB, drho, F.Fx, F.Fy, F.fm2, gn, rr, ux, uy);
             typename ST::T *dst = gout + (qy * p.pitch + c);
 #pragma unroll
             for (int i = 0; i < 9; i++) dst[i * (int)p.plane] = ST::pack(gn[i], i);
             chk += rr + ux + uy;
-            inv_rho = 1.0f / rho;
+            inv_rho = __fdividef(1.0f, rho);
           } else {
-            inv_rho = 1.0f / rho;
+            inv_rho = __fdividef(1.0f, rho);
             const float jx = (fB[1] - fB[3]) + (fB[5] - fB[7]) - (fB[6] - fB[8]);
             const float jy = (fB[2] - fB[4]) + (fB[5] - fB[7]) + (fB[6] - fB[8]);
             ux = (jx + 0.5f * F.Fx) * inv_rho;
@@ -262,8 +264,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             if (mirror) ring_u[sl + 1] = make_float2(ux, uy);
             if (mirror_in) ring_u[sl - 1] = make_float2(ux, uy);
             const float br = p.eos_b * rho;
-            ring_cf[sl] = make_float4(p.lam_cv * inv_rho, p.R_cv / (1.0f - br),
-                                      p.akap_cv * rho / (1.0f + 2.0f * br - br * br), 0.0f);
+            ring_cf[sl] = make_float4(p.lam_cv * inv_rho, __fdividef(p.R_cv, 1.0f - br),
+                                      __fdividef(p.akap_cv * rho, 1.0f + 2.0f * br - br * br),
+                                      0.0f);
           }
         }
       }
@@ -398,6 +401,16 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     }
     drhoB = drhoA;
     drhoA = drhoC;
+    {
+      const int a = q4[0];
+#pragma unroll
+      for (int d = 0; d < 3; d++) q4[d] = q4[d + 1];
+      q4[3] = a;
+      const int b = q8[0];
+#pragma unroll
+      for (int d = 0; d < 7; d++) q8[d] = q8[d + 1];
+      q8[7] = b;
+    }
 #undef R4
 #undef R8
     __syncthreads();
@@ -410,21 +423,23 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
 }
 
 template <bool YW, bool XO, bool TH, bool MP, class ST>
-__global__ void __launch_bounds__(FNT, 512 / FNT)
+__global__ void __launch_bounds__(FNT, LBM_FUSED_MIN_CTAS)
     k_fused_step(DevParams p, const typename ST::T *__restrict__ gs,
                  typename ST::T *__restrict__ gout, const float *__restrict__ Tin,
-                 float *__restrict__ Tout, unsigned *status, StepScalars sc, int H, int W) {
+                 float *__restrict__ Tout, unsigned *status, StepScalars sc, int nch, int W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
-  fused_tile<YW, XO, TH, MP, ST>(p, gs, gout, Tin, Tout, status, sc, blockIdx.x, blockIdx.y, H, W,
-                                 S);
+  // nch row chunks of nearly equal height (they differ by at most one row)
+  const int Y0 = (int)(((long long)blockIdx.y * p.ny) / nch);
+  const int ye = (int)(((long long)(blockIdx.y + 1) * p.ny) / nch);
+  fused_tile<YW, XO, TH, MP, ST>(p, gs, gout, Tin, Tout, status, sc, blockIdx.x * W, W, Y0, ye, S);
 }
 
 // Persistent batched update: resident CTAs take tiles of many lattices from one
 // work-list through an atomic counter (largest lattices first), so uneven lattice
 // sizes balance across the SMs.  The last CTA to leave resets the counters.
 template <bool YW, bool XO, bool TH, bool MP, class ST>
-__global__ void __launch_bounds__(FNT, 512 / FNT)
+__global__ void __launch_bounds__(FNT, LBM_FUSED_MIN_CTAS)
     k_fused_batch(const BatchChannel *__restrict__ ch, int nch, const StepScalars *__restrict__ sc,
                   int ntiles, int *counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -460,9 +475,10 @@ __global__ void __launch_bounds__(FNT, 512 / FNT)
     __syncthreads();
     const int local = tile - C.tile_begin;
     const int bx = local % C.strips, by = local / C.strips;
+    const int Y0 = by * C.H;
     fused_tile<YW, XO, TH, MP, ST>(sp, static_cast<const typename ST::T *>(C.gs),
                                    static_cast<typename ST::T *>(C.gout), C.Tin, C.Tout, C.status,
-                                   sc[s_ch], bx, by, C.H, C.W, S);
+                                   sc[s_ch], bx * C.W, C.W, Y0, min(Y0 + C.H, sp.ny), S);
     __syncthreads();
   }
   if (threadIdx.x == 0 && atomicAdd(&counter[1], 1) == (int)gridDim.x - 1) {
@@ -512,10 +528,11 @@ cudaError_t prepare(const DevParams &p, int *occ) {
 template <class ST>
 cudaError_t launch_t(const DevParams &p, const void *gs, void *gout, const float *Tin, float *Tout,
                      unsigned *status, StepScalars sc, FusedTiling tl, cudaStream_t s) {
-  dim3 grid((p.nx + tl.W - 1) / tl.W, (p.ny + tl.H - 1) / tl.H);
+  const int nch = (p.ny + tl.H - 1) / tl.H;
+  dim3 grid((p.nx + tl.W - 1) / tl.W, nch);
   fused_variant<ST>(p)<<<grid, FNT, sizeof(FusedSmem), s>>>(
       p, static_cast<const typename ST::T *>(gs), static_cast<typename ST::T *>(gout), Tin, Tout,
-      status, sc, tl.H, tl.W);
+      status, sc, nch, tl.W);
   return cudaGetLastError();
 }
 

@@ -77,11 +77,12 @@ __global__ void __launch_bounds__(BX *BY)
     }
     F = interaction_force(p, psi[c], dpsin, solid, psiw);
   }
-  const float rho_v = p.drho_ref_g + sum9(g);  // rho - rho_v of Eq. 15
+  const float drho = sum9(g);
+  const float rho_v = p.drho_ref_g + drho;  // rho - rho_v of Eq. 15
   F.Fx += rho_v * p.gx * sc.gcos;
   F.Fy += rho_v * p.gy * sc.gcos;
   float gn[9], rho, ux, uy;
-  collide(p, g, F.Fx, F.Fy, F.fm2, gn, rho, ux, uy);
+  collide(p, g, drho, F.Fx, F.Fy, F.fm2, gn, rho, ux, uy);
   if (WRITE_POP) {
 #pragma unroll
     for (int i = 0; i < 9; i++) gout[i * p.plane + c] = S::pack(gn[i], i);
