@@ -156,6 +156,15 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
   d.akap_cv = p.Cv > 0.0 ? (float)(p.eos_a * (0.37464 + 1.54226 * p.eos_omega -
                                              0.26992 * p.eos_omega * p.eos_omega) / p.Cv)
                          : 0.0f;
+  {
+    const double kap = 0.37464 + 1.54226 * p.eos_omega - 0.26992 * p.eos_omega * p.eos_omega;
+    const double akap = p.eos_a * kap;
+    d.lam23_cv = p.Cv > 0.0 ? (float)(2.0 * p.lambda / (3.0 * p.Cv)) : 0.0f;
+    d.RTc_cv3 = p.Cv > 0.0 ? (float)(p.eos_R * Tc / (3.0 * p.Cv)) : 0.0f;
+    d.akap1_cv3 = p.Cv > 0.0 ? (float)(akap * (1.0 + kap) / (3.0 * p.Cv)) : 0.0f;
+    d.kappa_r = (float)(kap / (1.0 + kap));
+    d.xr = (float)((double)d.T_ref / Tc);
+  }
   d.tw0 = (float)(Tc * p.T_wall_left - T_ref);
   d.tw_slope = nx > 1 ? (float)(Tc * (p.T_wall_right - p.T_wall_left) / (nx - 1)) : 0.0f;
   d.T_inlet_dev = (float)(Tc * p.T_inlet - T_ref);

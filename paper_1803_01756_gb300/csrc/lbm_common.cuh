@@ -99,6 +99,10 @@ struct DevParams {
   int has_g;              // gx or gy nonzero
   float Cv, lambda;
   float lam_cv, R_cv, akap_cv;  // lambda/Cv, R/Cv, a kappa/Cv
+  // energy coefficients of the fused kernel's RK4 stages (K(T) with the stencil and
+  // sqrt(T/Tc) factors folded in): (2/3) lambda/Cv, R Tc/(3 Cv), a kappa (1 + kappa)/(3 Cv),
+  // kappa/(1 + kappa), T_ref/Tc
+  float lam23_cv, RTc_cv3, akap1_cv3, kappa_r, xr;
   float tw0, tw_slope;    // wall temperature deviation at x: tw0 + tw_slope * x
   float T_inlet_dev;
   float rho_out;

@@ -36,10 +36,10 @@ constexpr int FW = FNT - 2 * FHALO;  // output columns per CTA
 struct FusedSmem {
   float psi[4][FNT];    // psi - psi_r, rows j-3 .. j
   float2 u[4][FNT];     // velocity, rows j-5 .. j-2
-  float4 cf[4][FNT];    // energy coefficients of rho (cl, cA, cB, -), same rows
+  float4 cf[4][FNT];    // energy coefficients of rho (cl, E1/(3 div u), E2/(3 div u), -), same rows
   float T[8][FNT];      // T - T_ref, rows j-5 .. j
   float T2[4][FNT], T3[4][FNT], T4[4][FNT];  // RK stage fields
-  // own-column values of rows j-10 .. j-4: (ux, uy, cl, e1), (e2, Tb) and the RK4 sum
+  // own-column values of rows j-10 .. j-4: (ux/3, uy/3, cl, E1), (E2, Tb) and the RK4 sum
   float4 o1[8][FNT];
   float2 o2[8][FNT];
   float oacc[8][FNT];
@@ -50,24 +50,27 @@ __device__ __forceinline__ int modi(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
-// K(T) of Eq. 16 at one node from a 3-row ring window of the stage field.
-//   grad = 3 sum w_i T(x+e_i) e_i,  lap = 6 sum w_i (T(x+e_i) - T(x)),
-//   K = -u.grad T + cl lap - e1 T - e2 s (1 + kappa - kappa s),  s = sqrt(T/Tc)
-// where cl = lambda/(rho Cv) and e1, e2 carry (dP/dT)_rho T div u / (rho Cv).
+// K(T) of Eq. 16 at one node from a 3-row ring window of the stage field, with
+//   grad T = 3 sum w_i T(x+e_i) e_i = g / 3,    g_x = (T1 - T3) + (T5 - T7 + T8 - T6) / 4,
+//   lap T = 6 sum w_i (T(x+e_i) - T(x)) = 2 L / 3,
+//                                         L = (T1 + T2 + T3 + T4 - 4T) + (T5 + T6 + T7 + T8 - 4T) / 4,
+//   T (dP/dT)_rho div u / (rho Cv) = e1 T + e2 s (1 + kappa - kappa s),  s = sqrt(T/Tc),
+// and, with x = T/Tc = s^2, the last term equal to E1 x + E2 s (E1 = e1 Tc - e2 kappa,
+// E2 = e2 (1 + kappa)).  The caller passes us = u/3, cl = (2/3) lambda/(rho Cv), E1, E2:
+//   K = -us.g + cl L - E1 x - E2 s.
 __device__ __forceinline__ float rk_rate(const DevParams &p, const float *__restrict__ R, int im,
-                                         int i0, int ip, float ux, float uy, float cl, float e1,
-                                         float e2) {
+                                         int i0, int ip, float uxs, float uys, float cl, float E1,
+                                         float E2) {
   const float c = R[i0];
   const float v1 = R[i0 + 1], v3 = R[i0 - 1], v2 = R[ip], v4 = R[im];
   const float v5 = R[ip + 1], v6 = R[ip - 1], v7 = R[im - 1], v8 = R[im + 1];
-  const float gx = (1.0f / 3.0f) * (v1 - v3) + (1.0f / 12.0f) * ((v5 - v7) + (v8 - v6));
-  const float gy = (1.0f / 3.0f) * (v2 - v4) + (1.0f / 12.0f) * ((v5 - v7) + (v6 - v8));
-  const float lap = (2.0f / 3.0f) * ((v1 + v3) + (v2 + v4) - 4.0f * c) +
-                    (1.0f / 6.0f) * ((v5 + v7) + (v6 + v8) - 4.0f * c);
-  const float Tabs = p.T_ref + c;
-  const float x = Tabs * p.inv_Tc;  // T > 0 on fluid nodes
+  const float d57 = v5 - v7;
+  const float gx = (v1 - v3) + 0.25f * (d57 + (v8 - v6));
+  const float gy = (v2 - v4) + 0.25f * (d57 + (v6 - v8));
+  const float lap = ((v1 + v3) + (v2 + v4) - 4.0f * c) + 0.25f * ((v5 + v7) + (v6 + v8) - 4.0f * c);
+  const float x = fmaf(c, p.inv_Tc, p.xr);  // T/Tc > 0 on fluid nodes
   const float s = x * rsqrtf(x);
-  return -(ux * gx + uy * gy) + cl * lap - e1 * Tabs - e2 * s * (1.0f + p.kappa - p.kappa * s);
+  return -(uxs * gx + uys * gy) + cl * lap - E1 * x - E2 * s;
 }
 
 // One tile of the fused update: output columns [X0, X0 + W) and rows [Y0, ye) of
@@ -128,10 +131,11 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
 
   unsigned st = 0;
   // running checks folded into status bits once at the end
+  // (on deviations; the references are added once at the end)
   float chk = 0.0f;         // NaN propagates through the sum
-  float rho_min = 1.0f;     // density must stay positive
-  float br_max = 0.0f;      // b rho must stay below the pole of Eq. 11
-  float T_min = 1.0f;       // absolute temperature must stay positive
+  float drho_min = 0.0f;    // density must stay positive
+  float drho_max = 0.0f;    // b rho must stay below the pole of Eq. 11
+  float dT_min = 0.0f;      // absolute temperature must stay positive
   float fA[9], fB[9];
   float drhoA = 0.0f, drhoB = 0.0f;  // density deviations of the two newest pulled rows
 #pragma unroll
@@ -250,7 +254,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             typename ST::T *dst = gout + (qy * p.pitch + c);
 #pragma unroll
             for (int i = 0; i < 9; i++) dst[i * (int)p.plane] = ST::pack(gn[i], i);
-            chk += rr + ux + uy;
+            chk += ux + uy;  // rho enters at S0
             inv_rho = __fdividef(1.0f, rho);
           } else {
             inv_rho = __fdividef(1.0f, rho);
@@ -263,10 +267,11 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             ring_u[sl] = make_float2(ux, uy);
             if (mirror) ring_u[sl + 1] = make_float2(ux, uy);
             if (mirror_in) ring_u[sl - 1] = make_float2(ux, uy);
+            // energy coefficients of the node (see rk_rate): cl, E1 / (3 div u), E2 / (3 div u)
             const float br = p.eos_b * rho;
-            ring_cf[sl] = make_float4(p.lam_cv * inv_rho, __fdividef(p.R_cv, 1.0f - br),
-                                      __fdividef(p.akap_cv * rho, 1.0f + 2.0f * br - br * br),
-                                      0.0f);
+            const float z = __fdividef(p.akap1_cv3 * rho, 1.0f + 2.0f * br - br * br);
+            ring_cf[sl] = make_float4(p.lam23_cv * inv_rho,
+                                      __fdividef(p.RTc_cv3, 1.0f - br) - p.kappa_r * z, z, 0.0f);
           }
         }
       }
@@ -288,20 +293,21 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             const float2 a1 = ring_u[u0 + 1], a3 = ring_u[u0 - 1], a2 = ring_u[up], a4 = ring_u[um];
             const float2 a5 = ring_u[up + 1], a6 = ring_u[up - 1], a7 = ring_u[um - 1],
                          a8 = ring_u[um + 1];
-            // div u = 3 sum w_i u(x+e_i).e_i
-            const float divu = (1.0f / 3.0f) * ((a1.x - a3.x) + (a2.y - a4.y)) +
-                               (1.0f / 12.0f) * ((a5.x + a5.y) - (a6.x - a6.y) -
-                                                 (a7.x + a7.y) + (a8.x - a8.y));
+            // 3 div u = 9 sum w_i u(x+e_i).e_i (the 1/3 is folded into the cf coefficients)
+            const float divu3 = ((a1.x - a3.x) + (a2.y - a4.y)) +
+                                0.25f * ((a5.x + a5.y) - (a6.x - a6.y) - (a7.x + a7.y) +
+                                         (a8.x - a8.y));
             const float2 uo = ring_u[u0];
             const float4 cf = ring_cf[u0];
-            const float e1 = cf.y * divu, e2 = cf.z * divu;
+            const float E1 = cf.y * divu3, E2 = cf.z * divu3;
+            const float uxs = uo.x * (1.0f / 3.0f), uys = uo.y * (1.0f / 3.0f);
             const int t0 = R8(4);
             const float Tb = ring_T[t0];
-            const float h1 = rk_rate(p, ring_T, R8(5), t0, R8(3), uo.x, uo.y, cf.x, e1, e2);
+            const float h1 = rk_rate(p, ring_T, R8(5), t0, R8(3), uxs, uys, cf.x, E1, E2);
             ring_T2[sl] = Tb + 0.5f * h1;
             if (mirror) ring_T2[sl + 1] = Tb + 0.5f * h1;
-            ring_o1[t0] = make_float4(uo.x, uo.y, cf.x, e1);
-            ring_o2[t0] = make_float2(e2, Tb);
+            ring_o1[t0] = make_float4(uxs, uys, cf.x, E1);
+            ring_o2[t0] = make_float2(E2, Tb);
             ring_acc[t0] = h1;
           }
         }
@@ -359,7 +365,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
                                    w2.x);
           const float Tn = w2.y + (ring_acc[o] + h4) * (1.0f / 6.0f);
           chk += Tn;
-          T_min = fminf(T_min, p.T_ref + Tn);
+          dT_min = fminf(dT_min, Tn);
           Tout[q * p.pitch + c] = Tn;
         }
       }
@@ -387,11 +393,10 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           ring_T[sT - 1] = p.T_inlet_dev;
           ring_psi[sl - 1] = dpsi;
         }
-        const float rho = p.rho_ref + drho;
-        rho_min = fminf(rho_min, rho);
-        br_max = fmaxf(br_max, p.eos_b * rho);
-        T_min = fminf(T_min, p.T_ref + Tc);
-        chk += rho;
+        drho_min = fminf(drho_min, drho);
+        drho_max = fmaxf(drho_max, drho);
+        dT_min = fminf(dT_min, Tc);
+        chk += drho;
       }
     }
 #pragma unroll
@@ -416,9 +421,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     __syncthreads();
   }
   if (!isfinite(chk)) st |= ST_NAN;
-  if (!(rho_min > 0.0f)) st |= ST_RHO_NONPOS;
-  if (!(br_max < 1.0f)) st |= ST_EOS_POLE;
-  if (!(T_min > 0.0f)) st |= ST_T_NONPOS;
+  if (!(p.rho_ref + drho_min > 0.0f)) st |= ST_RHO_NONPOS;
+  if (!(p.eos_b * (p.rho_ref + drho_max) < 1.0f)) st |= ST_EOS_POLE;
+  if (!(p.T_ref + dT_min > 0.0f)) st |= ST_T_NONPOS;
   set_status(status, st);
 }
 
