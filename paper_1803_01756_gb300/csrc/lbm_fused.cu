@@ -34,6 +34,7 @@ constexpr int FHALO = 5;             // psi is needed 5 nodes beyond the outputs
 constexpr int FW = FNT - 2 * FHALO;  // output columns per CTA
 
 struct FusedSmem {
+  float4 pad_lo;        // neighbour reads of thread 0 below the first ring
   float psi[4][FNT];    // psi - psi_r, rows j-3 .. j
   float2 u[4][FNT];     // velocity, rows j-5 .. j-2
   float4 cf[4][FNT];    // energy coefficients of rho (cl, E1/(3 div u), E2/(3 div u), -), same rows
@@ -43,6 +44,7 @@ struct FusedSmem {
   float4 o1[8][FNT];
   float2 o2[8][FNT];
   float oacc[8][FNT];
+  float4 pad_hi;        // neighbour reads of the last thread above the last ring
 };
 
 __device__ __forceinline__ int modi(int v, int n) {
@@ -153,6 +155,13 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
 #pragma unroll
   for (int d = 0; d < 8; d++) q8[d] = d * FNT + t;
 
+  // Stage conditions depend on the row only (uniform over the CTA).  Within a stage every
+  // thread computes, including halo threads outside the cone their stage is needed in
+  // (stage k is needed for dxo <= 5 - k) and ghost columns beyond an open end: those
+  // values are neither stored to global memory nor read by a needed column, and the
+  // ring writes that a boundary column mirrors into a ghost slot are predicated off in
+  // the ghost thread.  The pads around the rings keep the outermost threads' neighbour
+  // reads in bounds.
   const int J = (ye - Y0) + 3 * FHALO;
 #pragma unroll 1
   for (int j = 0; j < J; j++) {
@@ -177,30 +186,33 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     float fc[9];
     unsigned unk = 0u;
     float Tc = 0.0f, drhoC = 0.0f;
-    if (s0_row && !r_solid && !ghost) {
+    if (s0_row && !r_solid) {
+      // ghost threads load their clamped column (in bounds) and never use it
       const int own = ry * p.pitch + cx;
       if (ry > 0 && ry < p.ny - 1) {
         const typename ST::T *src = gs + own;
 #pragma unroll
         for (int i = 0; i < 9; i++) fc[i] = ST::load(src + poff[i], i);
-        unk = unk_edge;
+        unk = ghost ? 0u : unk_edge;
       } else {
         pull_load<ST>(p, gs, cx, ry, fc, unk);
+        if (ghost) unk = 0u;
       }
       Tc = __ldg(Tin + own);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; i++) fc[i] = 0.0f;
     }
 
     // ---------------- S1: row r-2 (forces, velocity, collision) ----------------
     {
       const int q = r - 2;
-      if (j >= 3 && q < ye + 4 && dxo <= 4) {
+      if (j >= 3 && q < ye + 4) {
         const int sl = R4(2);
         const bool solid = YW && (q < 0 || q >= p.ny);
         if (solid) {
           if (TH) ring_u[sl] = make_float2(0.0f, 0.0f);
-        } else if (col_in) {
-          if (TH && !p.p_inlet) ring_u[sl] = make_float2(sc.u_in, 0.0f);
-        } else if (!col_out) {
+        } else {
           const int qy = YW ? q : modi(q, p.ny);
           const float drho = drhoB;
           const float rho = p.rho_ref + drho;
@@ -247,26 +259,30 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             F.Fx += rho_v * p.gx * sc.gcos;
             F.Fy += rho_v * p.gy * sc.gcos;
           }
-          float ux, uy, inv_rho;
-          if (dxo == 0 && q >= Y0 && q < ye) {
+          float ux, uy;
+          const float inv_rho = __fdividef(1.0f, rho);
+          if (q >= Y0 && q < ye) {
             float gn[9], rr;
             collide(p, fB, drho, F.Fx, F.Fy, F.fm2, gn, rr, ux, uy);
-            typename ST::T *dst = gout + (qy * p.pitch + c);
+            if (dxo == 0) {
+              typename ST::T *dst = gout + (qy * p.pitch + c);
 #pragma unroll
-            for (int i = 0; i < 9; i++) dst[i * (int)p.plane] = ST::pack(gn[i], i);
-            chk += ux + uy;  // rho enters at S0
-            inv_rho = __fdividef(1.0f, rho);
+              for (int i = 0; i < 9; i++) dst[i * (int)p.plane] = ST::pack(gn[i], i);
+              chk += ux + uy;  // rho enters at S0
+            }
           } else {
-            inv_rho = __fdividef(1.0f, rho);
             const float jx = (fB[1] - fB[3]) + (fB[5] - fB[7]) - (fB[6] - fB[8]);
             const float jy = (fB[2] - fB[4]) + (fB[5] - fB[7]) + (fB[6] - fB[8]);
             ux = (jx + 0.5f * F.Fx) * inv_rho;
             uy = (jy + 0.5f * F.Fy) * inv_rho;
           }
           if (TH) {
-            ring_u[sl] = make_float2(ux, uy);
-            if (mirror) ring_u[sl + 1] = make_float2(ux, uy);
-            if (mirror_in) ring_u[sl - 1] = make_float2(ux, uy);
+            // the velocity inlet's ghost holds the inlet velocity; with a pressure inlet
+            // column 0 mirrors its velocity there
+            const float2 uu = col_in ? make_float2(sc.u_in, 0.0f) : make_float2(ux, uy);
+            if (!col_out && !(col_in && p.p_inlet)) ring_u[sl] = uu;
+            if (mirror) ring_u[sl + 1] = uu;
+            if (mirror_in) ring_u[sl - 1] = uu;
             // energy coefficients of the node (see rk_rate): cl, E1 / (3 div u), E2 / (3 div u)
             const float br = p.eos_b * rho;
             const float z = __fdividef(p.akap1_cv3 * rho, 1.0f + 2.0f * br - br * br);
@@ -281,14 +297,12 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       // ---------------- S2: row r-4 (div u, h1) ----------------
       {
         const int q = r - 4;
-        if (j >= 6 && q < ye + 3 && dxo <= 3) {
+        if (j >= 6 && q < ye + 3) {
           const int sl = R4(4);
           const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
             ring_T2[sl] = twall;
-          } else if (col_in) {
-            ring_T2[sl] = p.T_inlet_dev;
-          } else if (!col_out) {
+          } else {
             const int um = R4(5), u0 = R4(4), up = R4(3);
             const float2 a1 = ring_u[u0 + 1], a3 = ring_u[u0 - 1], a2 = ring_u[up], a4 = ring_u[um];
             const float2 a5 = ring_u[up + 1], a6 = ring_u[up - 1], a7 = ring_u[um - 1],
@@ -304,8 +318,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             const int t0 = R8(4);
             const float Tb = ring_T[t0];
             const float h1 = rk_rate(p, ring_T, R8(5), t0, R8(3), uxs, uys, cf.x, E1, E2);
-            ring_T2[sl] = Tb + 0.5f * h1;
-            if (mirror) ring_T2[sl + 1] = Tb + 0.5f * h1;
+            const float v = col_in ? p.T_inlet_dev : Tb + 0.5f * h1;
+            if (!col_out) ring_T2[sl] = v;
+            if (mirror) ring_T2[sl + 1] = v;
             ring_o1[t0] = make_float4(uxs, uys, cf.x, E1);
             ring_o2[t0] = make_float2(E2, Tb);
             ring_acc[t0] = h1;
@@ -315,20 +330,19 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       // ---------------- S3: row r-6 (h2) ----------------
       {
         const int q = r - 6;
-        if (j >= 9 && q < ye + 2 && dxo <= 2) {
+        if (j >= 9 && q < ye + 2) {
           const int sl = R4(6);
           const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
             ring_T3[sl] = twall;
-          } else if (col_in) {
-            ring_T3[sl] = p.T_inlet_dev;
-          } else if (!col_out) {
+          } else {
             const int o = R8(6);
             const float4 w1 = ring_o1[o];
             const float2 w2 = ring_o2[o];
             const float h2 = rk_rate(p, ring_T2, R4(7), sl, R4(5), w1.x, w1.y, w1.z, w1.w, w2.x);
-            ring_T3[sl] = w2.y + 0.5f * h2;
-            if (mirror) ring_T3[sl + 1] = w2.y + 0.5f * h2;
+            const float v = col_in ? p.T_inlet_dev : w2.y + 0.5f * h2;
+            if (!col_out) ring_T3[sl] = v;
+            if (mirror) ring_T3[sl + 1] = v;
             ring_acc[o] += 2.0f * h2;
           }
         }
@@ -336,20 +350,19 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       // ---------------- S4: row r-8 (h3) ----------------
       {
         const int q = r - 8;
-        if (j >= 12 && q < ye + 1 && dxo <= 1) {
+        if (j >= 12 && q < ye + 1) {
           const int sl = R4(8);
           const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
             ring_T4[sl] = twall;
-          } else if (col_in) {
-            ring_T4[sl] = p.T_inlet_dev;
-          } else if (!col_out) {
+          } else {
             const int o = R8(8);
             const float4 w1 = ring_o1[o];
             const float2 w2 = ring_o2[o];
             const float h3 = rk_rate(p, ring_T3, R4(9), sl, R4(7), w1.x, w1.y, w1.z, w1.w, w2.x);
-            ring_T4[sl] = w2.y + h3;
-            if (mirror) ring_T4[sl + 1] = w2.y + h3;
+            const float v = col_in ? p.T_inlet_dev : w2.y + h3;
+            if (!col_out) ring_T4[sl] = v;
+            if (mirror) ring_T4[sl + 1] = v;
             ring_acc[o] += 2.0f * h3;
           }
         }
@@ -357,16 +370,18 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       // ---------------- S5: row r-10 (h4, new temperature) ----------------
       {
         const int q = r - 10;
-        if (j >= 15 && q < ye && dxo == 0) {
+        if (j >= 15 && q < ye) {
           const int o = R8(10);
           const float4 w1 = ring_o1[o];
           const float2 w2 = ring_o2[o];
           const float h4 = rk_rate(p, ring_T4, R4(11), R4(10), R4(9), w1.x, w1.y, w1.z, w1.w,
                                    w2.x);
           const float Tn = w2.y + (ring_acc[o] + h4) * (1.0f / 6.0f);
-          chk += Tn;
-          dT_min = fminf(dT_min, Tn);
-          Tout[q * p.pitch + c] = Tn;
+          if (dxo == 0) {
+            chk += Tn;
+            dT_min = fminf(dT_min, Tn);
+            Tout[q * p.pitch + c] = Tn;
+          }
         }
       }
     }
@@ -377,14 +392,22 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       if (r_solid) {
         ring_T[sT] = twall;
         ring_psi[sl] = 0.0f;
-      } else if (!ghost) {
+      } else {
         pull_fix(p, cx, sc, fc, unk);
-        ring_T[sT] = Tc;
         float dpsi = 0.0f;
         const float drho = sum9(fc);
         drhoC = drho;
-        if (MP) dpsi = pseudopotential_dev(p, drho, Tc, st);
-        ring_psi[sl] = dpsi;
+        unsigned st_psi = 0u;
+        if (MP) dpsi = pseudopotential_dev(p, drho, Tc, st_psi);
+        if (!ghost) {
+          st |= st_psi;  // a ghost's populations include unfixed placeholders
+          ring_T[sT] = Tc;
+          ring_psi[sl] = dpsi;
+          drho_min = fminf(drho_min, drho);
+          drho_max = fmaxf(drho_max, drho);
+          dT_min = fminf(dT_min, Tc);
+          chk += drho;
+        }
         if (mirror) {
           ring_T[sT + 1] = Tc;
           ring_psi[sl + 1] = dpsi;
@@ -393,10 +416,6 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           ring_T[sT - 1] = p.T_inlet_dev;
           ring_psi[sl - 1] = dpsi;
         }
-        drho_min = fminf(drho_min, drho);
-        drho_max = fmaxf(drho_max, drho);
-        dT_min = fminf(dT_min, Tc);
-        chk += drho;
       }
     }
 #pragma unroll
@@ -431,13 +450,15 @@ template <bool YW, bool XO, bool TH, bool MP, class ST>
 __global__ void __launch_bounds__(FNT, LBM_FUSED_MIN_CTAS)
     k_fused_step(DevParams p, const typename ST::T *__restrict__ gs,
                  typename ST::T *__restrict__ gout, const float *__restrict__ Tin,
-                 float *__restrict__ Tout, unsigned *status, StepScalars sc, int nch, int W) {
+                 float *__restrict__ Tout, unsigned *status, StepScalars sc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
-  // nch row chunks of nearly equal height (they differ by at most one row)
-  const int Y0 = (int)(((long long)blockIdx.y * p.ny) / nch);
-  const int ye = (int)(((long long)(blockIdx.y + 1) * p.ny) / nch);
-  fused_tile<YW, XO, TH, MP, ST>(p, gs, gout, Tin, Tout, status, sc, blockIdx.x * W, W, Y0, ye, S);
+  // strips and row chunks of nearly equal size (they differ by at most one column or row)
+  const int X0 = (int)(((long long)blockIdx.x * p.nx) / gridDim.x);
+  const int X1 = (int)(((long long)(blockIdx.x + 1) * p.nx) / gridDim.x);
+  const int Y0 = (int)(((long long)blockIdx.y * p.ny) / gridDim.y);
+  const int ye = (int)(((long long)(blockIdx.y + 1) * p.ny) / gridDim.y);
+  fused_tile<YW, XO, TH, MP, ST>(p, gs, gout, Tin, Tout, status, sc, X0, X1 - X0, Y0, ye, S);
 }
 
 // Persistent batched update: resident CTAs take tiles of many lattices from one
@@ -503,7 +524,7 @@ namespace {
 
 template <class ST>
 using FusedFn = void (*)(DevParams, const typename ST::T *, typename ST::T *, const float *,
-                         float *, unsigned *, StepScalars, int, int);
+                         float *, unsigned *, StepScalars);
 
 template <class ST>
 FusedFn<ST> fused_variant(const DevParams &p) {
@@ -533,11 +554,11 @@ cudaError_t prepare(const DevParams &p, int *occ) {
 template <class ST>
 cudaError_t launch_t(const DevParams &p, const void *gs, void *gout, const float *Tin, float *Tout,
                      unsigned *status, StepScalars sc, FusedTiling tl, cudaStream_t s) {
-  const int nch = (p.ny + tl.H - 1) / tl.H;
-  dim3 grid((p.nx + tl.W - 1) / tl.W, nch);
+  // ceil(nx / W) strips of at most W columns and ceil(ny / H) chunks of at most H rows
+  dim3 grid((p.nx + tl.W - 1) / tl.W, (p.ny + tl.H - 1) / tl.H);
   fused_variant<ST>(p)<<<grid, FNT, sizeof(FusedSmem), s>>>(
       p, static_cast<const typename ST::T *>(gs), static_cast<typename ST::T *>(gout), Tin, Tout,
-      status, sc, nch, tl.W);
+      status, sc);
   return cudaGetLastError();
 }
 
