@@ -52,6 +52,13 @@ __device__ __forceinline__ int modi(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// Shared-memory ring access by a byte offset `off` of a float element (slot * FNT * 4 +
+// column * 4; +-4 for the neighbouring columns); rings of float2 and float4 elements
+// scale it by their element size, so one offset register serves every ring.
+#define F1(ring, off) (*reinterpret_cast<float *>(reinterpret_cast<char *>(ring) + (off)))
+#define F2(ring, off) (*reinterpret_cast<float2 *>(reinterpret_cast<char *>(ring) + 2 * (off)))
+#define F4(ring, off) (*reinterpret_cast<float4 *>(reinterpret_cast<char *>(ring) + 4 * (off)))
+
 // K(T) of Eq. 16 at one node from a 3-row ring window of the stage field, with
 //   grad T = 3 sum w_i T(x+e_i) e_i = g / 3,    g_x = (T1 - T3) + (T5 - T7 + T8 - T6) / 4,
 //   lap T = 6 sum w_i (T(x+e_i) - T(x)) = 2 L / 3,
@@ -60,12 +67,12 @@ __device__ __forceinline__ int modi(int v, int n) {
 // and, with x = T/Tc = s^2, the last term equal to E1 x + E2 s (E1 = e1 Tc - e2 kappa,
 // E2 = e2 (1 + kappa)).  The caller passes us = u/3, cl = (2/3) lambda/(rho Cv), E1, E2:
 //   K = -us.g + cl L - E1 x - E2 s.
-__device__ __forceinline__ float rk_rate(const DevParams &p, const float *__restrict__ R, int im,
+__device__ __forceinline__ float rk_rate(const DevParams &p, float *__restrict__ R, int im,
                                          int i0, int ip, float uxs, float uys, float cl, float E1,
                                          float E2) {
-  const float c = R[i0];
-  const float v1 = R[i0 + 1], v3 = R[i0 - 1], v2 = R[ip], v4 = R[im];
-  const float v5 = R[ip + 1], v6 = R[ip - 1], v7 = R[im - 1], v8 = R[im + 1];
+  const float c = F1(R, i0);
+  const float v1 = F1(R, i0 + 4), v3 = F1(R, i0 - 4), v2 = F1(R, ip), v4 = F1(R, im);
+  const float v5 = F1(R, ip + 4), v6 = F1(R, ip - 4), v7 = F1(R, im - 4), v8 = F1(R, im + 4);
   const float d57 = v5 - v7;
   const float gx = (v1 - v3) + 0.25f * (d57 + (v8 - v6));
   const float gy = (v2 - v4) + 0.25f * (d57 + (v6 - v8));
@@ -146,14 +153,14 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     fB[i] = 0.0f;
   }
 
-  // element index of ring row (j - k) at this thread's column, shared by every ring and
-  // stage (R4(k), R8(k) below): q4[d] = ((j + d) & 3) FNT + t, q8[d] = ((j + d) & 7) FNT + t,
-  // rotated by one position per row step
+  // float byte offset of ring row (j - k) at this thread's column, shared by every ring
+  // and stage (R4(k), R8(k) below): q4[d] = 4 (((j + d) & 3) FNT + t),
+  // q8[d] = 4 (((j + d) & 7) FNT + t), rotated by one position per row step
   int q4[4], q8[8];
 #pragma unroll
-  for (int d = 0; d < 4; d++) q4[d] = d * FNT + t;
+  for (int d = 0; d < 4; d++) q4[d] = 4 * (d * FNT + t);
 #pragma unroll
-  for (int d = 0; d < 8; d++) q8[d] = d * FNT + t;
+  for (int d = 0; d < 8; d++) q8[d] = 4 * (d * FNT + t);
 
   // Stage conditions depend on the row only (uniform over the CTA).  Within a stage every
   // thread computes, including halo threads outside the cone their stage is needed in
@@ -211,7 +218,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
         const int sl = R4(2);
         const bool solid = YW && (q < 0 || q >= p.ny);
         if (solid) {
-          if (TH) ring_u[sl] = make_float2(0.0f, 0.0f);
+          if (TH) F2(ring_u, sl) = make_float2(0.0f, 0.0f);
         } else {
           const int qy = YW ? q : modi(q, p.ny);
           const float drho = drhoB;
@@ -223,15 +230,15 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             const bool sup = YW && q + 1 >= p.ny;
             float dn[9];
             dn[0] = 0.0f;
-            dn[1] = ring_psi[p0 + 1];
-            dn[2] = ring_psi[pp];
-            dn[3] = ring_psi[p0 - 1];
-            dn[4] = ring_psi[pm];
-            dn[5] = ring_psi[pp + 1];
-            dn[6] = ring_psi[pp - 1];
-            dn[7] = ring_psi[pm - 1];
-            dn[8] = ring_psi[pm + 1];
-            const float dpc = ring_psi[p0];
+            dn[1] = F1(ring_psi, p0 + 4);
+            dn[2] = F1(ring_psi, pp);
+            dn[3] = F1(ring_psi, p0 - 4);
+            dn[4] = F1(ring_psi, pm);
+            dn[5] = F1(ring_psi, pp + 4);
+            dn[6] = F1(ring_psi, pp - 4);
+            dn[7] = F1(ring_psi, pm - 4);
+            dn[8] = F1(ring_psi, pm + 4);
+            const float dpc = F1(ring_psi, p0);
             if (!sdn && !sup) {
               // no wall neighbour: F = -G psi sum w dpsi e  (Eq. 9; sum w e = 0)
               const float qx = (1.0f / 3.0f) * (dn[1] - dn[3]) +
@@ -249,7 +256,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
               float psiw = 0.0f;
               if (p.rho_w > 0.0f) {
                 unsigned st_unused = 0;
-                psiw = pseudopotential(p, p.rho_w, p.T_ref + ring_T[R8(2)], st_unused);
+                psiw = pseudopotential(p, p.rho_w, p.T_ref + F1(ring_T, R8(2)), st_unused);
               }
               F = interaction_force(p, dpc, dn, solid_mask, psiw);
             }
@@ -280,13 +287,13 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             // the velocity inlet's ghost holds the inlet velocity; with a pressure inlet
             // column 0 mirrors its velocity there
             const float2 uu = col_in ? make_float2(sc.u_in, 0.0f) : make_float2(ux, uy);
-            if (!col_out && !(col_in && p.p_inlet)) ring_u[sl] = uu;
-            if (mirror) ring_u[sl + 1] = uu;
-            if (mirror_in) ring_u[sl - 1] = uu;
+            if (!col_out && !(col_in && p.p_inlet)) F2(ring_u, sl) = uu;
+            if (mirror) F2(ring_u, sl + 4) = uu;
+            if (mirror_in) F2(ring_u, sl - 4) = uu;
             // energy coefficients of the node (see rk_rate): cl, E1 / (3 div u), E2 / (3 div u)
             const float br = p.eos_b * rho;
             const float z = __fdividef(p.akap1_cv3 * rho, 1.0f + 2.0f * br - br * br);
-            ring_cf[sl] = make_float4(p.lam23_cv * inv_rho,
+            F4(ring_cf, sl) = make_float4(p.lam23_cv * inv_rho,
                                       __fdividef(p.RTc_cv3, 1.0f - br) - p.kappa_r * z, z, 0.0f);
           }
         }
@@ -301,29 +308,30 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           const int sl = R4(4);
           const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
-            ring_T2[sl] = twall;
+            F1(ring_T2, sl) = twall;
           } else {
             const int um = R4(5), u0 = R4(4), up = R4(3);
-            const float2 a1 = ring_u[u0 + 1], a3 = ring_u[u0 - 1], a2 = ring_u[up], a4 = ring_u[um];
-            const float2 a5 = ring_u[up + 1], a6 = ring_u[up - 1], a7 = ring_u[um - 1],
-                         a8 = ring_u[um + 1];
+            const float2 a1 = F2(ring_u, u0 + 4), a3 = F2(ring_u, u0 - 4);
+            const float2 a2 = F2(ring_u, up), a4 = F2(ring_u, um);
+            const float2 a5 = F2(ring_u, up + 4), a6 = F2(ring_u, up - 4);
+            const float2 a7 = F2(ring_u, um - 4), a8 = F2(ring_u, um + 4);
             // 3 div u = 9 sum w_i u(x+e_i).e_i (the 1/3 is folded into the cf coefficients)
             const float divu3 = ((a1.x - a3.x) + (a2.y - a4.y)) +
                                 0.25f * ((a5.x + a5.y) - (a6.x - a6.y) - (a7.x + a7.y) +
                                          (a8.x - a8.y));
-            const float2 uo = ring_u[u0];
-            const float4 cf = ring_cf[u0];
+            const float2 uo = F2(ring_u, u0);
+            const float4 cf = F4(ring_cf, u0);
             const float E1 = cf.y * divu3, E2 = cf.z * divu3;
             const float uxs = uo.x * (1.0f / 3.0f), uys = uo.y * (1.0f / 3.0f);
             const int t0 = R8(4);
-            const float Tb = ring_T[t0];
+            const float Tb = F1(ring_T, t0);
             const float h1 = rk_rate(p, ring_T, R8(5), t0, R8(3), uxs, uys, cf.x, E1, E2);
             const float v = col_in ? p.T_inlet_dev : Tb + 0.5f * h1;
-            if (!col_out) ring_T2[sl] = v;
-            if (mirror) ring_T2[sl + 1] = v;
-            ring_o1[t0] = make_float4(uxs, uys, cf.x, E1);
-            ring_o2[t0] = make_float2(E2, Tb);
-            ring_acc[t0] = h1;
+            if (!col_out) F1(ring_T2, sl) = v;
+            if (mirror) F1(ring_T2, sl + 4) = v;
+            F4(ring_o1, t0) = make_float4(uxs, uys, cf.x, E1);
+            F2(ring_o2, t0) = make_float2(E2, Tb);
+            F1(ring_acc, t0) = h1;
           }
         }
       }
@@ -334,16 +342,16 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           const int sl = R4(6);
           const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
-            ring_T3[sl] = twall;
+            F1(ring_T3, sl) = twall;
           } else {
             const int o = R8(6);
-            const float4 w1 = ring_o1[o];
-            const float2 w2 = ring_o2[o];
+            const float4 w1 = F4(ring_o1, o);
+            const float2 w2 = F2(ring_o2, o);
             const float h2 = rk_rate(p, ring_T2, R4(7), sl, R4(5), w1.x, w1.y, w1.z, w1.w, w2.x);
             const float v = col_in ? p.T_inlet_dev : w2.y + 0.5f * h2;
-            if (!col_out) ring_T3[sl] = v;
-            if (mirror) ring_T3[sl + 1] = v;
-            ring_acc[o] += 2.0f * h2;
+            if (!col_out) F1(ring_T3, sl) = v;
+            if (mirror) F1(ring_T3, sl + 4) = v;
+            F1(ring_acc, o) += 2.0f * h2;
           }
         }
       }
@@ -354,16 +362,16 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           const int sl = R4(8);
           const bool solid = YW && (q < 0 || q >= p.ny);
           if (solid) {
-            ring_T4[sl] = twall;
+            F1(ring_T4, sl) = twall;
           } else {
             const int o = R8(8);
-            const float4 w1 = ring_o1[o];
-            const float2 w2 = ring_o2[o];
+            const float4 w1 = F4(ring_o1, o);
+            const float2 w2 = F2(ring_o2, o);
             const float h3 = rk_rate(p, ring_T3, R4(9), sl, R4(7), w1.x, w1.y, w1.z, w1.w, w2.x);
             const float v = col_in ? p.T_inlet_dev : w2.y + h3;
-            if (!col_out) ring_T4[sl] = v;
-            if (mirror) ring_T4[sl + 1] = v;
-            ring_acc[o] += 2.0f * h3;
+            if (!col_out) F1(ring_T4, sl) = v;
+            if (mirror) F1(ring_T4, sl + 4) = v;
+            F1(ring_acc, o) += 2.0f * h3;
           }
         }
       }
@@ -372,11 +380,11 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
         const int q = r - 10;
         if (j >= 15 && q < ye) {
           const int o = R8(10);
-          const float4 w1 = ring_o1[o];
-          const float2 w2 = ring_o2[o];
+          const float4 w1 = F4(ring_o1, o);
+          const float2 w2 = F2(ring_o2, o);
           const float h4 = rk_rate(p, ring_T4, R4(11), R4(10), R4(9), w1.x, w1.y, w1.z, w1.w,
                                    w2.x);
-          const float Tn = w2.y + (ring_acc[o] + h4) * (1.0f / 6.0f);
+          const float Tn = w2.y + (F1(ring_acc, o) + h4) * (1.0f / 6.0f);
           if (dxo == 0) {
             chk += Tn;
             dT_min = fminf(dT_min, Tn);
@@ -390,8 +398,8 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     if (s0_row) {
       const int sl = R4(0), sT = R8(0);
       if (r_solid) {
-        ring_T[sT] = twall;
-        ring_psi[sl] = 0.0f;
+        F1(ring_T, sT) = twall;
+        F1(ring_psi, sl) = 0.0f;
       } else {
         pull_fix(p, cx, sc, fc, unk);
         float dpsi = 0.0f;
@@ -401,20 +409,20 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
         if (MP) dpsi = pseudopotential_dev(p, drho, Tc, st_psi);
         if (!ghost) {
           st |= st_psi;  // a ghost's populations include unfixed placeholders
-          ring_T[sT] = Tc;
-          ring_psi[sl] = dpsi;
+          F1(ring_T, sT) = Tc;
+          F1(ring_psi, sl) = dpsi;
           drho_min = fminf(drho_min, drho);
           drho_max = fmaxf(drho_max, drho);
           dT_min = fminf(dT_min, Tc);
           chk += drho;
         }
         if (mirror) {
-          ring_T[sT + 1] = Tc;
-          ring_psi[sl + 1] = dpsi;
+          F1(ring_T, sT + 4) = Tc;
+          F1(ring_psi, sl + 4) = dpsi;
         }
         if (mirror_in0) {
-          ring_T[sT - 1] = p.T_inlet_dev;
-          ring_psi[sl - 1] = dpsi;
+          F1(ring_T, sT - 4) = p.T_inlet_dev;
+          F1(ring_psi, sl - 4) = dpsi;
         }
       }
     }
