@@ -169,7 +169,11 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
   // ring writes that a boundary column mirrors into a ghost slot are predicated off in
   // the ghost thread.  The pads around the rings keep the outermost threads' neighbour
   // reads in bounds.
-  const int J = (ye - Y0) + 3 * FHALO;
+  // Row ranges as one unsigned compare each: stage k (S1..S5) runs for 3k <= j < HR + 10 + k,
+  // S0 for j < HR + 10, where HR is the number of output rows.
+  const int HR = ye - Y0;
+  const unsigned uny = (unsigned)p.ny;
+  const int J = HR + 3 * FHALO;
 #pragma unroll 1
   for (int j = 0; j < J; j++) {
     const int r = Y0 - FHALO + j;
@@ -187,8 +191,8 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     float *const ring_acc = &S.oacc[0][0];
 
     // ---------------- S0 loads: row r ----------------
-    const bool s0_row = r < ye + FHALO;
-    const bool r_solid = YW && (r < 0 || r >= p.ny);
+    const bool s0_row = j < HR + 2 * FHALO;
+    const bool r_solid = YW && (unsigned)r >= uny;
     const int ry = YW ? r : modi(r, p.ny);
     float fc[9];
     unsigned unk = 0u;
@@ -196,7 +200,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     if (s0_row && !r_solid) {
       // ghost threads load their clamped column (in bounds) and never use it
       const int own = ry * p.pitch + cx;
-      if (ry > 0 && ry < p.ny - 1) {
+      if ((unsigned)(ry - 1) < (unsigned)(p.ny - 2)) {  // 0 < ry < ny - 1
         const typename ST::T *src = gs + own;
 #pragma unroll
         for (int i = 0; i < 9; i++) fc[i] = ST::load(src + poff[i], i);
@@ -214,9 +218,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     // ---------------- S1: row r-2 (forces, velocity, collision) ----------------
     {
       const int q = r - 2;
-      if (j >= 3 && q < ye + 4) {
+      if ((unsigned)(j - 3) < (unsigned)(HR + 8)) {
         const int sl = R4(2);
-        const bool solid = YW && (q < 0 || q >= p.ny);
+        const bool solid = YW && (unsigned)q >= uny;
         if (solid) {
           if (TH) F2(ring_u, sl) = make_float2(0.0f, 0.0f);
         } else {
@@ -226,8 +230,8 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           Force F{0.0f, 0.0f, 0.0f};
           if (MP) {
             const int pm = R4(3), p0 = R4(2), pp = R4(1);
-            const bool sdn = YW && q - 1 < 0;
-            const bool sup = YW && q + 1 >= p.ny;
+            const bool sdn = YW && q == 0;  // q is a fluid row here
+            const bool sup = YW && q == p.ny - 1;
             float dn[9];
             dn[0] = 0.0f;
             dn[1] = F1(ring_psi, p0 + 4);
@@ -268,7 +272,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           }
           float ux, uy;
           const float inv_rho = __fdividef(1.0f, rho);
-          if (q >= Y0 && q < ye) {
+          if ((unsigned)(q - Y0) < (unsigned)HR) {
             float gn[9], rr;
             collide(p, fB, drho, F.Fx, F.Fy, F.fm2, gn, rr, ux, uy);
             if (dxo == 0) {
@@ -304,9 +308,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       // ---------------- S2: row r-4 (div u, h1) ----------------
       {
         const int q = r - 4;
-        if (j >= 6 && q < ye + 3) {
+        if ((unsigned)(j - 6) < (unsigned)(HR + 6)) {
           const int sl = R4(4);
-          const bool solid = YW && (q < 0 || q >= p.ny);
+          const bool solid = YW && (unsigned)q >= uny;
           if (solid) {
             F1(ring_T2, sl) = twall;
           } else {
@@ -338,9 +342,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       // ---------------- S3: row r-6 (h2) ----------------
       {
         const int q = r - 6;
-        if (j >= 9 && q < ye + 2) {
+        if ((unsigned)(j - 9) < (unsigned)(HR + 4)) {
           const int sl = R4(6);
-          const bool solid = YW && (q < 0 || q >= p.ny);
+          const bool solid = YW && (unsigned)q >= uny;
           if (solid) {
             F1(ring_T3, sl) = twall;
           } else {
@@ -358,9 +362,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       // ---------------- S4: row r-8 (h3) ----------------
       {
         const int q = r - 8;
-        if (j >= 12 && q < ye + 1) {
+        if ((unsigned)(j - 12) < (unsigned)(HR + 2)) {
           const int sl = R4(8);
-          const bool solid = YW && (q < 0 || q >= p.ny);
+          const bool solid = YW && (unsigned)q >= uny;
           if (solid) {
             F1(ring_T4, sl) = twall;
           } else {
@@ -378,7 +382,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
       // ---------------- S5: row r-10 (h4, new temperature) ----------------
       {
         const int q = r - 10;
-        if (j >= 15 && q < ye) {
+        if ((unsigned)(j - 15) < (unsigned)HR) {
           const int o = R8(10);
           const float4 w1 = F4(ring_o1, o);
           const float2 w2 = F2(ring_o2, o);
