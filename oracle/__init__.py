@@ -45,6 +45,9 @@ class OrcParams(ctypes.Structure):
         ("rho_out", ctypes.c_double),
         ("thermal", ctypes.c_int), ("multiphase", ctypes.c_int),
         ("p_amp_frac", ctypes.c_double),
+        ("T_top_left", ctypes.c_double), ("T_top_right", ctypes.c_double),
+        ("top_iso_x0", ctypes.c_int), ("top_iso_x1", ctypes.c_int),
+        ("bot_iso_x0", ctypes.c_int), ("bot_iso_x1", ctypes.c_int),
     ]
 
 

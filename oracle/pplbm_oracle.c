@@ -26,8 +26,11 @@
  *    applied, without force, to the populations that enter from outside the x
  *    range through fluid rows; wall-row links are bounced back first.
  *  - Energy-equation ghosts: wall rows hold the wall temperature (linear in x
- *    between the two given end values) and zero velocity; the inlet ghost holds
- *    T_inlet and the inlet velocity; the outlet ghost copies the last column.
+ *    between the two given end values, the top wall optionally with its own
+ *    values) and zero velocity; on adiabatic wall columns (Section 3.2: outside a
+ *    wall's isothermal window) the ghost copies the fluid node across the wall;
+ *    the inlet ghost holds T_inlet and the inlet velocity; the outlet ghost copies
+ *    the last column.
  *  - Pressure inlet (Section 3.3): the inlet pressure p0 (1 + a sin(2 pi t/P)) is
  *    imposed through the density whose Peng-Robinson pressure at T_inlet equals it,
  *    taken on the vapour branch (below the first maximum of P(rho)); p0 is the
@@ -328,10 +331,25 @@ static double inlet_velocity(const orc_lattice *L, long t) {
   return L->p.u_amp * sin(2.0 * PI * (double)t / L->p.u_period);
 }
 
-/* wall temperature, linear between the end values along x (units of Tc -> absolute) */
-static double wall_temperature(const orc_lattice *L, int x) {
+/* wall temperature, linear between the end values along x (units of Tc -> absolute);
+   the top wall has its own profile when one of its end values is set */
+static double wall_temperature(const orc_lattice *L, int x, int top) {
   double s = L->nx > 1 ? (double)x / (double)(L->nx - 1) : 0.0;
-  return L->Tc * (L->p.T_wall_left + s * (L->p.T_wall_right - L->p.T_wall_left));
+  double a = L->p.T_wall_left, b = L->p.T_wall_right;
+  if (top && (L->p.T_top_left != 0.0 || L->p.T_top_right != 0.0)) {
+    a = L->p.T_top_left;
+    b = L->p.T_top_right;
+  }
+  return L->Tc * (a + s * (b - a));
+}
+
+/* 1 when column x of the top (or bottom) wall is adiabatic: outside the wall's
+   isothermal window [x0, x1); an empty window (x1 <= x0) makes the whole wall isothermal */
+static int wall_adiabatic(const orc_lattice *L, int x, int top) {
+  int x0 = top ? L->p.top_iso_x0 : L->p.bot_iso_x0;
+  int x1 = top ? L->p.top_iso_x1 : L->p.bot_iso_x1;
+  if (x1 <= x0) return 0;
+  return x < x0 || x >= x1;
 }
 
 /* ------------------------------------------------------------------ */
@@ -485,7 +503,13 @@ static void macroscopic(orc_lattice *L) {
 static double ghost_T(const orc_lattice *L, const double *Tf, int x, int y, int i) {
   int xo, yo;
   int k = classify(L, x, y, EX[i], EY[i], &xo, &yo);
-  if (k == NB_SOLID) return wall_temperature(L, xo);
+  if (k == NB_SOLID) {
+    /* isothermal: the wall temperature; adiabatic: the fluid node across the wall
+       (the ghost mirrors the first fluid row, so the normal gradient vanishes) */
+    int top = y + EY[i] >= L->ny;
+    if (wall_adiabatic(L, xo, top)) return Tf[(top ? L->ny - 1 : 0) * L->nx + xo];
+    return wall_temperature(L, xo, top);
+  }
   if (k == NB_INLET) return L->Tc * L->p.T_inlet;
   return Tf[yo * L->nx + xo]; /* fluid, or outlet copy */
 }

@@ -52,6 +52,14 @@ typedef struct orc_params {
   int thermal;                           /* 1: advance T by Eqs. 16-18 */
   int multiphase;                        /* 1: pseudopotential forces of Eqs. 9, 14 */
   double p_amp_frac;                     /* pressure inlet: p = p0 (1 + p_amp_frac sin(2 pi t/u_period)) */
+  /* Section 3.2 walls: the top wall's temperature profile (units of Tc, linear in x;
+     both 0 means the profile of T_wall_left/right) and, per wall, the columns
+     [x0, x1) that are isothermal; the rest of that wall is adiabatic (zero normal
+     gradient of T: the energy-equation ghost copies the fluid node across the wall).
+     x1 <= x0: the whole wall is isothermal. */
+  double T_top_left, T_top_right;
+  int top_iso_x0, top_iso_x1;
+  int bot_iso_x0, bot_iso_x1;
 } orc_params;
 
 typedef struct orc_lattice orc_lattice;
