@@ -79,6 +79,14 @@ typedef struct lbm_params {
   double p_amp_frac;                     /* pressure inlet (Section 3.3): p = p0 (1 + p_amp_frac
                                             sin(2 pi t / u_period)), p0 = P_EOS(rho_out, T_inlet),
                                             imposed as the vapour-branch density of that pressure */
+  /* Section 3.2 walls.  The top wall's temperature profile (units of Tc, linear in x; both 0
+     selects T_wall_left/right for the top wall too) and, per wall, the columns [x0, x1) that
+     are isothermal; the rest of that wall is adiabatic: the energy equation's ghost copies the
+     fluid node across the wall (zero normal gradient of T).  x1 <= x0 makes the whole wall
+     isothermal.  Adiabatic columns need periodic x ends (LBM_ERR_ARG otherwise). */
+  double T_top_left, T_top_right;
+  int top_iso_x0, top_iso_x1;
+  int bot_iso_x0, bot_iso_x1;
 } lbm_params_t;
 
 typedef struct lbm_lattice *lbm_h;

@@ -269,12 +269,17 @@ enum { NB_FLUID = 0, NB_SOLID = 1, NB_INLET = 2, NB_OUTLET = 3 };
 
 /* Classify site (x+dx, y+dy) seen from a fluid node.  Wall rows are tested
    first.  For fluid, inlet-ghost and outlet-ghost sites (*xo, *yo) is the
-   fluid node that supplies a copied value (wrapped, or clamped at open ends). */
+   fluid node that supplies a copied value (wrapped, or clamped at open ends);
+   for a wall site, *xo is its column (the periodic image when x is periodic,
+   clamped at open ends) and *yo the fluid row next to the wall. */
 static int classify(const orc_lattice *L, int x, int y, int dx, int dy, int *xo, int *yo) {
   int xs = x + dx, ys = y + dy;
   if (L->p.y_bc == ORC_Y_WALLS) {
     if (ys < 0 || ys >= L->ny) {
-      *xo = xs < 0 ? 0 : (xs >= L->nx ? L->nx - 1 : xs);
+      if (L->p.x_bc == ORC_X_PERIODIC)
+        *xo = wrap(xs, L->nx);
+      else
+        *xo = xs < 0 ? 0 : (xs >= L->nx ? L->nx - 1 : xs);
       *yo = ys < 0 ? 0 : L->ny - 1;
       return NB_SOLID;
     }

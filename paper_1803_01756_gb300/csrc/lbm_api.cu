@@ -69,6 +69,10 @@ int validate(int nx, int ny, const lbm_params_t &p) {
     return LBM_ERR_ARG;
   if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_FUSED) return LBM_ERR_ARG;
   if (p.u_period < 0.0 || std::fabs(p.u_amp) >= 1.0) return LBM_ERR_ARG;
+  // adiabatic wall columns (outside a non-empty isothermal window) only with periodic x
+  const bool adia = (p.top_iso_x1 > p.top_iso_x0 && (p.top_iso_x0 > 0 || p.top_iso_x1 < nx)) ||
+                    (p.bot_iso_x1 > p.bot_iso_x0 && (p.bot_iso_x0 > 0 || p.bot_iso_x1 < nx));
+  if (adia && (p.x_bc != LBM_X_PERIODIC || p.y_bc != LBM_Y_WALLS)) return LBM_ERR_ARG;
   return LBM_OK;
 }
 
@@ -167,6 +171,19 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
   }
   d.tw0 = (float)(Tc * p.T_wall_left - T_ref);
   d.tw_slope = nx > 1 ? (float)(Tc * (p.T_wall_right - p.T_wall_left) / (nx - 1)) : 0.0f;
+  {
+    const bool own = p.T_top_left != 0.0 || p.T_top_right != 0.0;
+    const double a = own ? p.T_top_left : p.T_wall_left, b = own ? p.T_top_right : p.T_wall_right;
+    d.tw0_top = (float)(Tc * a - T_ref);
+    d.tw_slope_top = nx > 1 ? (float)(Tc * (b - a) / (nx - 1)) : 0.0f;
+  }
+  d.top_iso_x0 = p.top_iso_x0;
+  d.top_iso_x1 = p.top_iso_x1;
+  d.bot_iso_x0 = p.bot_iso_x0;
+  d.bot_iso_x1 = p.bot_iso_x1;
+  d.adiabatic = p.y_bc == LBM_Y_WALLS &&
+                ((p.top_iso_x1 > p.top_iso_x0 && (p.top_iso_x0 > 0 || p.top_iso_x1 < nx)) ||
+                 (p.bot_iso_x1 > p.bot_iso_x0 && (p.bot_iso_x0 > 0 || p.bot_iso_x1 < nx)));
   d.T_inlet_dev = (float)(Tc * p.T_inlet - T_ref);
   d.rho_out = (float)p.rho_out;
   return d;

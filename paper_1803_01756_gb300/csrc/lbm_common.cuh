@@ -103,7 +103,12 @@ struct DevParams {
   // sqrt(T/Tc) factors folded in): (2/3) lambda/Cv, R Tc/(3 Cv), a kappa (1 + kappa)/(3 Cv),
   // kappa/(1 + kappa), T_ref/Tc
   float lam23_cv, RTc_cv3, akap1_cv3, kappa_r, xr;
-  float tw0, tw_slope;    // wall temperature deviation at x: tw0 + tw_slope * x
+  float tw0, tw_slope;    // wall temperature deviation at x: tw0 + tw_slope * x (bottom wall)
+  float tw0_top, tw_slope_top;  // the same for the top wall
+  // isothermal windows [x0, x1) of the two walls; outside them the wall is adiabatic
+  // (x1 <= x0: isothermal everywhere); adiabatic != 0 when some column is adiabatic
+  int top_iso_x0, top_iso_x1, bot_iso_x0, bot_iso_x1;
+  int adiabatic;
   float T_inlet_dev;
   float rho_out;
 };
@@ -192,7 +197,7 @@ __device__ __forceinline__ int classify(const DevParams &p, int x, int y, int dx
   int xs = x + dx, ys = y + dy;
   if (p.y_walls) {
     if (ys < 0 || ys >= p.ny) {
-      xo = min(max(xs, 0), p.nx - 1);
+      xo = p.x_open ? min(max(xs, 0), p.nx - 1) : wrapi(xs, p.nx);
       yo = ys < 0 ? 0 : p.ny - 1;
       return NB_SOLID;
     }
@@ -396,6 +401,17 @@ __device__ __forceinline__ void collide(const DevParams &p, const float g[9], fl
 __device__ __forceinline__ float wall_T_dev(const DevParams &p, int x) {
   x = min(max(x, 0), p.nx - 1);
   return p.tw0 + p.tw_slope * (float)x;
+}
+
+__device__ __forceinline__ float wall_T_top_dev(const DevParams &p, int x) {
+  x = min(max(x, 0), p.nx - 1);
+  return p.tw0_top + p.tw_slope_top * (float)x;
+}
+
+// column x of the top (bottom) wall is adiabatic: outside the wall's isothermal window
+__device__ __forceinline__ bool wall_adiabatic(const DevParams &p, int x, bool top) {
+  const int x0 = top ? p.top_iso_x0 : p.bot_iso_x0, x1 = top ? p.top_iso_x1 : p.bot_iso_x1;
+  return x1 > x0 && (x < x0 || x >= x1);
 }
 
 }  // namespace lbm

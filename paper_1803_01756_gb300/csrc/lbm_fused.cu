@@ -118,7 +118,14 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
   const bool mirror = XO && c == p.nx - 1 && t + 1 < FNT;
   const bool mirror_in0 = XO && c == 0 && t >= 1;
   const bool mirror_in = mirror_in0 && p.p_inlet;
-  const float twall = wall_T_dev(p, cx);
+  // Energy-equation ghosts of the walls (Section 3.2): isothermal columns hold the wall
+  // temperature of their wall; on adiabatic columns every stage field's ghost copies the
+  // fluid node across the wall: at the top the ghost row takes the value of row ny - 1
+  // written one row step earlier, at the bottom row 0 writes its value into the slot of
+  // row -1 (not read by any stage before then).  Adiabatic columns come with periodic x.
+  const float twall = wall_T_dev(p, cx), twall_top = wall_T_top_dev(p, cx);
+  const bool adi_bot = YW && p.adiabatic && wall_adiabatic(p, cx, false);
+  const bool adi_top = YW && p.adiabatic && wall_adiabatic(p, cx, true);
 
   // Pull offsets relative to the node's own index (Eq. 12, f_i(x) = f*_i(x - e_i)), used
   // on every row not next to a wall.  Next to a periodic seam the source column wraps;
@@ -312,7 +319,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           const int sl = R4(4);
           const bool solid = YW && (unsigned)q >= uny;
           if (solid) {
-            F1(ring_T2, sl) = twall;
+            F1(ring_T2, sl) = q < 0 ? twall : (adi_top ? F1(ring_T2, R4(5)) : twall_top);
           } else {
             const int um = R4(5), u0 = R4(4), up = R4(3);
             const float2 a1 = F2(ring_u, u0 + 4), a3 = F2(ring_u, u0 - 4);
@@ -333,6 +340,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             const float v = col_in ? p.T_inlet_dev : Tb + 0.5f * h1;
             if (!col_out) F1(ring_T2, sl) = v;
             if (mirror) F1(ring_T2, sl + 4) = v;
+            if (adi_bot && q == 0) F1(ring_T2, R4(5)) = v;
             F4(ring_o1, t0) = make_float4(uxs, uys, cf.x, E1);
             F2(ring_o2, t0) = make_float2(E2, Tb);
             F1(ring_acc, t0) = h1;
@@ -346,7 +354,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           const int sl = R4(6);
           const bool solid = YW && (unsigned)q >= uny;
           if (solid) {
-            F1(ring_T3, sl) = twall;
+            F1(ring_T3, sl) = q < 0 ? twall : (adi_top ? F1(ring_T3, R4(7)) : twall_top);
           } else {
             const int o = R8(6);
             const float4 w1 = F4(ring_o1, o);
@@ -355,6 +363,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             const float v = col_in ? p.T_inlet_dev : w2.y + 0.5f * h2;
             if (!col_out) F1(ring_T3, sl) = v;
             if (mirror) F1(ring_T3, sl + 4) = v;
+            if (adi_bot && q == 0) F1(ring_T3, R4(7)) = v;
             F1(ring_acc, o) += 2.0f * h2;
           }
         }
@@ -366,7 +375,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           const int sl = R4(8);
           const bool solid = YW && (unsigned)q >= uny;
           if (solid) {
-            F1(ring_T4, sl) = twall;
+            F1(ring_T4, sl) = q < 0 ? twall : (adi_top ? F1(ring_T4, R4(9)) : twall_top);
           } else {
             const int o = R8(8);
             const float4 w1 = F4(ring_o1, o);
@@ -375,6 +384,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
             const float v = col_in ? p.T_inlet_dev : w2.y + h3;
             if (!col_out) F1(ring_T4, sl) = v;
             if (mirror) F1(ring_T4, sl + 4) = v;
+            if (adi_bot && q == 0) F1(ring_T4, R4(9)) = v;
             F1(ring_acc, o) += 2.0f * h3;
           }
         }
@@ -402,7 +412,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
     if (s0_row) {
       const int sl = R4(0), sT = R8(0);
       if (r_solid) {
-        F1(ring_T, sT) = twall;
+        F1(ring_T, sT) = r < 0 ? twall : (adi_top ? F1(ring_T, R8(1)) : twall_top);
         F1(ring_psi, sl) = 0.0f;
       } else {
         pull_fix(p, cx, sc, fc, unk);
@@ -428,6 +438,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const typename ST
           F1(ring_T, sT - 4) = p.T_inlet_dev;
           F1(ring_psi, sl - 4) = dpsi;
         }
+        if (adi_bot && r == 0) F1(ring_T, R8(1)) = Tc;
       }
     }
 #pragma unroll

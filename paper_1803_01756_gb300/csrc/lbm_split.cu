@@ -127,7 +127,15 @@ __global__ void __launch_bounds__(ETHREADS)
     bool load = true;
     if (p.y_walls && (gy < 0 || gy >= p.ny)) {
       kind = K_WALL;
-      T = wall_T_dev(p, gx);
+      const bool top = gy >= p.ny;
+      const int wx = p.x_open ? gx : modi(gx, p.nx);  // periodic image of the wall column
+      if (p.adiabatic && wall_adiabatic(p, wx, top)) {
+        // adiabatic: every stage reads the fluid node across the wall (same column);
+        // x is periodic here, so that node lies inside this tile's halo region
+        red = ((top ? p.ny - 1 : 0) - y0) * ERX + lx;
+      } else {
+        T = top ? wall_T_top_dev(p, wx) : wall_T_dev(p, wx);
+      }
       load = false;
     } else {
       if (!p.y_walls) gy = modi(gy, p.ny);

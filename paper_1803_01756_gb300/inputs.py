@@ -97,6 +97,17 @@ WORKLOADS = {
     "channel_4096x512": dict(nx=4096, ny=512,
                              params=base_params(u_amp=0.03, u_period=10000.0),
                              seed=2, noise=0.01, steps=20000),
+    # Section 3.2: condensation on a cold wall under gravity, 100 x 300, periodic in x;
+    # the top wall is at 0.65 Tc on its middle half and adiabatic beside it, the bottom
+    # wall isothermal at the vapour's 0.86 Tc, gravity 1e-4 toward the bottom, walls
+    # hydrophobic (G_w = -1.10, about 109 degrees)
+    "condensation_100x300": dict(nx=100, ny=300,
+                                 params=base_params(x_bc=X_PERIODIC, u_amp=0.0, gy=-1e-4,
+                                                    Gw=-1.10, T_wall_left=0.86,
+                                                    T_wall_right=0.86, T_top_left=0.65,
+                                                    T_top_right=0.65, top_iso_x0=25,
+                                                    top_iso_x1=75),
+                                 seed=4, noise=0.01, steps=20000),
 }
 
 

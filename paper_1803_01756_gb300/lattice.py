@@ -46,6 +46,9 @@ class LbmParams(ctypes.Structure):
         ("thermal", ctypes.c_int), ("multiphase", ctypes.c_int),
         ("storage", ctypes.c_int), ("rho_ref", ctypes.c_double), ("kernel", ctypes.c_int),
         ("p_amp_frac", ctypes.c_double),
+        ("T_top_left", ctypes.c_double), ("T_top_right", ctypes.c_double),
+        ("top_iso_x0", ctypes.c_int), ("top_iso_x1", ctypes.c_int),
+        ("bot_iso_x0", ctypes.c_int), ("bot_iso_x1", ctypes.c_int),
     ]
 
 

@@ -97,6 +97,13 @@ CASES = [
     (400, 38, dict(y_bc=0, x_bc=0)),
     (390, 36, dict(x_bc=2, p_amp_frac=0.1, u_period=60.0, gx=1e-4)),
     (380, 34, dict(thermal=0, x_bc=0)),
+    # Section 3.2 walls: top wall colder on a window of columns and adiabatic beside it,
+    # bottom isothermal, gravity along -y, periodic x (narrow and multi-strip)
+    (48, 30, dict(x_bc=0, u_amp=0.0, gy=-1e-4, Gw=-1.10, T_wall_left=0.86, T_wall_right=0.86,
+                  T_top_left=0.65, T_top_right=0.65, top_iso_x0=12, top_iso_x1=36)),
+    (300, 26, dict(x_bc=0, u_amp=0.0, gy=-1e-4, T_wall_left=0.86, T_wall_right=0.80,
+                   T_top_left=0.70, T_top_right=0.75, top_iso_x0=100, top_iso_x1=200,
+                   bot_iso_x0=30, bot_iso_x1=280)),
 ]
 
 
@@ -147,6 +154,24 @@ def test_wide_channel_with_liquid(kernel):
     gpu, ref = run_both(nx, ny, p, rho0, 100, kernel)
     err = rel_errors(gpu, ref)
     assert max(err.values()) <= TOL, err
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_condensation_100x300(kernel):
+    """The Section 3.2 condensation workload at full size (cold top window, adiabatic
+    top beside it, gravity), 300 updates from seeded saturated vapour."""
+    w = inputs.workload("condensation_100x300")
+    gpu, ref = run_both(w["nx"], w["ny"], w["params"], inputs.initial_density(w), 300, kernel)
+    err = rel_errors(gpu, ref)
+    assert max(err.values()) <= TOL, err
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_adiabatic_walls_need_periodic_x(kernel):
+    from paper_1803_01756_gb300.lattice import Lattice, LbmError
+    p = inputs.base_params(top_iso_x0=4, top_iso_x1=10)  # open x ends
+    with pytest.raises(LbmError):
+        Lattice(32, 16, p, kernel=kernel_id(kernel))
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
