@@ -188,8 +188,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
   const int HR = ye - Y0;
   const unsigned uny = (unsigned)pg.ny;
   const int J = HR + 3 * FHALO;
-#pragma unroll 1
-  for (int j = 0; j < J; j++) {
+  // two row steps per iteration, so that the compiler renames the rotated registers within
+  // the pair (a step past J, when J is odd, runs no stage: every stage range ends by J)
+  auto row_step = [&](const int j) {
     const int r = Y0 - FHALO + j;
 #define R4(k) q4[(4 - ((k) & 3)) & 3]
 #define R8(k) q8[(8 - ((k) & 7)) & 7]
@@ -467,6 +468,12 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
     }
 #undef R4
 #undef R8
+  };
+#pragma unroll 1
+  for (int j = 0; j < J; j += 2) {
+    row_step(j);
+    __syncthreads();
+    row_step(j + 1);
     __syncthreads();
   }
   if (!isfinite(chk)) st |= ST_NAN;
