@@ -40,7 +40,7 @@ L2_BYTES = 129e6
 # DRAM bytes (read + write) of one k_fused_step launch on the 4096 x 512 channel with
 # FP32 storage, from ncu (profiles/k_fused_step_channel_4096x512.md); reported only
 # for that kernel, workload and storage.  Re-measure whenever the kernel changes.
-FUSED_F32_4096x512_DRAM_BYTES = 109.480960e6 + 40.918784e6
+FUSED_F32_4096x512_DRAM_BYTES = 109.544192e6 + 41.230080e6
 
 
 def env_int(name, default):
