@@ -288,7 +288,7 @@ def our_arm(args, world, rank, local, dist):
         dt = max_over_ranks(dt, dist)
         e2e = {"value": world * cells * inner * reps / dt / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": 8 * cells / inner,
-               "d2h_bytes_per_step": 4 * 4 * info["pitch"] * ny / inner,
+               "d2h_bytes_per_step": 4 * 8 * cells / inner,
                "job": f"write_fields (host rho) + {inner} updates + read_fields (host rho,u,T)"}
     lat.close()
 

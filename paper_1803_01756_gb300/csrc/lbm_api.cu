@@ -344,7 +344,6 @@ void free_all(lbm_lattice *h) {
   cudaFree(h->partials);
   cudaFree(h->sums);
   cudaFree(h->rho0);
-  if (h->host_stage) cudaFreeHost(h->host_stage);
   if (h->host_sums) cudaFreeHost(h->host_sums);
   for (auto &tl : h->pending) {
     cudaEventDestroy(tl.a);
@@ -361,20 +360,19 @@ cudaError_t dalloc(lbm_lattice *h, T **ptr, size_t count) {
   return e;
 }
 
+// Host fields in: rho (and T) go to the device staging array as they are, and kernels
+// form the populations and the pitched FP32 temperature deviations there; the stream
+// orders the reuse of the staging array.
 int upload_fields(lbm_lattice *h, const double *rho, const double *T, cudaStream_t s) {
   const size_t n = (size_t)h->nx * h->ny;
   LBM_CUDA(cudaMemcpyAsync(h->rho0, rho, n * sizeof(double), cudaMemcpyHostToDevice, s));
   LBM_CUDA(lbm::launch_init(h->dp, h->p.storage, h->rho0, h->g[h->cur], s));
-  // temperature deviations through the pinned staging buffer
-  float *st = h->host_stage;
-  LBM_CUDA(cudaStreamSynchronize(s));
-  for (int y = 0; y < h->ny; y++)
-    for (int x = 0; x < h->pitch; x++) {
-      double v = 0.0;
-      if (T && x < h->nx) v = T[(size_t)y * h->nx + x] - h->T_ref;
-      st[(size_t)y * h->pitch + x] = (float)v;
-    }
-  LBM_CUDA(cudaMemcpyAsync(h->T[h->tcur], st, sizeof(float) * h->plane, cudaMemcpyHostToDevice, s));
+  if (T) {
+    LBM_CUDA(cudaMemcpyAsync(h->rho0, T, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    LBM_CUDA(lbm::launch_pitch_T(h->rho0, h->nx, h->ny, h->pitch, h->T_ref, h->T[h->tcur], s));
+  } else {
+    LBM_CUDA(cudaMemsetAsync(h->T[h->tcur], 0, sizeof(float) * h->plane, s));
+  }
   LBM_CUDA(cudaStreamSynchronize(s));
   return LBM_OK;
 }
@@ -454,7 +452,6 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
   if (e == cudaSuccess) e = dalloc(h, &h->partials, 2 * (size_t)h->nblocks);
   if (e == cudaSuccess) e = dalloc(h, &h->sums, 2);
   if (e == cudaSuccess) e = dalloc(h, &h->rho0, (size_t)nx * ny);
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_stage, sizeof(float) * plane);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_sums, 2 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(unsigned));
   // padding columns stay zero forever
@@ -531,15 +528,15 @@ int lbm_read_fields(lbm_h h, double *rho, double *ux, double *uy, double *T, voi
     const float *src;
     double add;
   } outs[4] = {{rho, h->rho, 0.0}, {ux, h->ux, 0.0}, {uy, h->uy, 0.0}, {T, h->T[h->tcur], h->T_ref}};
+  // each field is widened to FP64 in the caller's layout in the device staging array
+  // and copied out; the stream orders the reuse of the array
+  const size_t n = (size_t)h->nx * h->ny;
   for (auto &o : outs) {
     if (!o.dst) continue;
-    LBM_CUDA(cudaMemcpyAsync(h->host_stage, o.src, sizeof(float) * h->plane,
-                             cudaMemcpyDeviceToHost, s));
-    LBM_CUDA(cudaStreamSynchronize(s));
-    for (int y = 0; y < h->ny; y++)
-      for (int x = 0; x < h->nx; x++)
-        o.dst[(size_t)y * h->nx + x] = (double)h->host_stage[(size_t)y * h->pitch + x] + o.add;
+    LBM_CUDA(lbm::launch_unpitch(o.src, h->nx, h->ny, h->pitch, o.add, h->rho0, s));
+    LBM_CUDA(cudaMemcpyAsync(o.dst, h->rho0, n * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
+  LBM_CUDA(cudaStreamSynchronize(s));
   unsigned bits = 0;
   rc = lbm_status(h, &bits, 0, stream);
   if (rc) return rc;

@@ -95,7 +95,37 @@ __global__ void __launch_bounds__(RT)
   }
 }
 
+__global__ void k_unpitch(const float *__restrict__ src, int nx, int ny, int pitch, double add,
+                          double *__restrict__ dst) {
+  const int x = blockIdx.x * IBX + threadIdx.x, y = blockIdx.y * IBY + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  dst[(long long)y * nx + x] = (double)src[(long long)y * pitch + x] + add;
+}
+
+__global__ void k_pitch_T(const double *__restrict__ T, int nx, int ny, int pitch, double T_ref,
+                          float *__restrict__ dst) {
+  const int x = blockIdx.x * IBX + threadIdx.x, y = blockIdx.y * IBY + threadIdx.y;
+  if (x >= pitch || y >= ny) return;
+  double v = 0.0;
+  if (x < nx) v = T[(long long)y * nx + x] - T_ref;
+  dst[(long long)y * pitch + x] = (float)v;
+}
+
 }  // namespace
+
+cudaError_t launch_unpitch(const float *src, int nx, int ny, int pitch, double add, double *dst,
+                           cudaStream_t s) {
+  dim3 grid((nx + IBX - 1) / IBX, (ny + IBY - 1) / IBY);
+  k_unpitch<<<grid, dim3(IBX, IBY), 0, s>>>(src, nx, ny, pitch, add, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pitch_T(const double *T, int nx, int ny, int pitch, double T_ref, float *dst,
+                           cudaStream_t s) {
+  dim3 grid((pitch + IBX - 1) / IBX, (ny + IBY - 1) / IBY);
+  k_pitch_T<<<grid, dim3(IBX, IBY), 0, s>>>(T, nx, ny, pitch, T_ref, dst);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_init(const DevParams &p, int storage, const double *rho0, void *gout,
                         cudaStream_t s) {

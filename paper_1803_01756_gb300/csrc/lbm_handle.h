@@ -38,8 +38,7 @@ struct lbm_lattice {
   unsigned *status = nullptr;
   double *partials = nullptr, *sums = nullptr;
   int nblocks = 1;
-  double *rho0 = nullptr;  // device staging for lbm_write_fields
-  float *host_stage = nullptr;  // pinned, plane floats
+  double *rho0 = nullptr;  // device staging (nx * ny doubles) for the field copies in and out
   double *host_sums = nullptr;  // pinned, 2 doubles
   size_t device_bytes = 0;
   // timing

@@ -64,5 +64,12 @@ cudaError_t launch_mass_heat(const DevParams &p, const float *rho, const float *
                              double T_ref, double Cv, double *partials, int nblocks,
                              double *out, cudaStream_t s);
 int mass_heat_blocks(const DevParams &p);
+// field conversion between the pitched FP32 planes and the caller's [ny][nx] FP64 layout:
+// dst[y][x] = src[y * pitch + x] + add, and (T may be NULL for a zero deviation)
+// dst[y * pitch + x] = T[y][x] - T_ref with zero padding columns
+cudaError_t launch_unpitch(const float *src, int nx, int ny, int pitch, double add, double *dst,
+                           cudaStream_t s);
+cudaError_t launch_pitch_T(const double *T, int nx, int ny, int pitch, double T_ref, float *dst,
+                           cudaStream_t s);
 
 }  // namespace lbm
