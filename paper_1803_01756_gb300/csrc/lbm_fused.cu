@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(FNT, LBM_FUSED_MIN_CTAS)
   const int X1 = (int)(((long long)(blockIdx.x + 1) * p.nx) / gridDim.x);
   const int Y0 = (int)(((long long)blockIdx.y * p.ny) / gridDim.y);
   const int ye = (int)(((long long)(blockIdx.y + 1) * p.ny) / gridDim.y);
-  fused_tile<YW, XO, TH, MP, ST>(p, p, gs, gout, Tin, Tout, status, sc, X0, X1 - X0, Y0, ye, S);
+  fused_tile<YW, XO, TH, MP, ST, 2>(p, p, gs, gout, Tin, Tout, status, sc, X0, X1 - X0, Y0, ye, S);
 }
 
 }  // namespace
