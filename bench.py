@@ -38,8 +38,9 @@ SPLIT_KERNEL_BYTES = {"k_density_psi": 36 + 4 + 8, "k_collide": 36 + 4 + 36 + 8,
                       "k_energy": 4 + 4 + 8 + 4, "k_fused_step": 80}
 L2_BYTES = 129e6
 # DRAM bytes (read + write) of one k_fused_step launch on the 4096 x 512 channel with
-# FP32 storage, from ncu (profiles/k_fused_step_channel_4096x512.md); reported only
-# for that kernel, workload and storage.  Re-measure whenever the kernel changes.
+# FP32 storage, measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch); reported only for that kernel, workload and storage.  Re-measure whenever the
+# kernel changes.
 FUSED_F32_4096x512_DRAM_BYTES = 109.544192e6 + 41.230080e6
 
 
