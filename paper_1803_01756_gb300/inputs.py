@@ -97,6 +97,10 @@ WORKLOADS = {
     "channel_4096x512": dict(nx=4096, ny=512,
                              params=base_params(u_amp=0.03, u_period=10000.0),
                              seed=2, noise=0.01, steps=20000),
+    # 16384 x 2048 channel: 2.4 GB of FP32 populations, far beyond L2
+    "channel_16384x2048": dict(nx=16384, ny=2048,
+                               params=base_params(u_amp=0.03, u_period=10000.0),
+                               seed=5, noise=0.01, steps=2000),
     # Section 3.2: condensation on a cold wall under gravity, 100 x 300, periodic in x;
     # the top wall is at 0.65 Tc on its middle half and adiabatic beside it, the bottom
     # wall isothermal at the vapour's 0.86 Tc, gravity 1e-4 toward the bottom, walls

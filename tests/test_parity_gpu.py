@@ -203,6 +203,26 @@ def test_full_size_long_run_properties(kernel):
     assert heat == pytest.approx((rho * w["params"]["Cv"] * T).sum(), rel=1e-6)
 
 
+def test_beyond_l2_channel_16384x2048():
+    """16384 x 2048 (2.4 GB of FP32 populations): the fused and the split kernels, each
+    held to the oracle at the sizes above, agree after 20 updates, with no status bits and
+    the FP64 mass reduction equal to the sum of the density field.  (The oracle would take
+    about 15 s and 8 GB of host memory per update at this size.)"""
+    w = inputs.workload("channel_16384x2048")
+    out = {}
+    for kernel in KERNELS:
+        lat = make_lattice(w["nx"], w["ny"], w["params"], kernel)
+        lat.write_fields(inputs.initial_density(w))
+        lat.step(20)
+        out[kernel] = lat.read_fields()
+        mass, _ = lat.reduce()
+        assert lat.status() == 0
+        lat.close()
+        assert mass == pytest.approx(out[kernel][0].sum(), rel=1e-12)
+    err = rel_errors(out["fused"], out["split"])
+    assert max(err.values()) <= TOL, err
+
+
 def test_mass_reduction_matches_oracle():
     nx, ny = 40, 24
     p = inputs.base_params(x_bc=0)
