@@ -171,7 +171,9 @@ int lbm_batch_create(lbm_h *lattices, int n, lbm_batch_h *out);
 int lbm_batch_step(lbm_batch_h b, long nsteps, void *stream);
 /* enable != 0: replay whole chunks of 16 steps from one captured CUDA graph. */
 int lbm_batch_set_graph(lbm_batch_h b, int enable);
-/* Output rows per tile (the work-list granularity; default 64). */
+/* Output rows per tile (the work-list granularity).  The default, chosen at creation, is the
+   height among 128, 96, 64, 48, 32, 24, 16 rows whose work-list a greedy schedule over the
+   resident CTAs finishes first. */
 int lbm_batch_set_tile_rows(lbm_batch_h b, int rows);
 /* Time tile heights 16..128 rows with steps_per_candidate timed updates each (plus two
    warm-up updates) and keep the fastest.  These are real updates: every lattice

@@ -104,3 +104,20 @@ def test_autotune_picks_a_candidate_and_keeps_results_finite():
     b.close()
     for lat in lats:
         lat.close()
+
+
+def test_default_tile_height_follows_the_batch_size():
+    """A few small lattices get short tiles (so that more CTAs get work: every tile sweeps
+    H + 15 row steps whatever the batch size), one large lattice taller ones."""
+    from paper_1803_01756_gb300.lattice import Batch, Lattice
+    small = [Lattice(512, 64, inputs.base_params(), kernel=2) for _ in range(12)]
+    b = Batch(small)
+    assert b.info()["tile_rows"] == 16
+    b.close()
+    big = Lattice(4096, 512, inputs.base_params(), kernel=2)
+    b = Batch([big])
+    info = b.info()
+    assert info["tile_rows"] >= 24 and info["tiles"] <= info["grid"]
+    b.close()
+    for lat in small + [big]:
+        lat.close()
