@@ -14,7 +14,8 @@ constexpr int IBX = 32, IBY = 8;
 template <class S>
 __global__ void k_init(DevParams p, const double *__restrict__ rho0,
                        typename S::T *__restrict__ gout) {
-  const int x = blockIdx.x * IBX + threadIdx.x, y = blockIdx.y * IBY + threadIdx.y;
+  const int tx = ceil_div(p.nx, IBX);
+  const int x = (int)(blockIdx.x % tx) * IBX + threadIdx.x, y = (int)(blockIdx.x / tx) * IBY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   const long long c = (long long)y * p.pitch + x;
   const double own = rho0[(long long)y * p.nx + x];
@@ -97,14 +98,16 @@ __global__ void __launch_bounds__(RT)
 
 __global__ void k_unpitch(const float *__restrict__ src, int nx, int ny, int pitch, double add,
                           double *__restrict__ dst) {
-  const int x = blockIdx.x * IBX + threadIdx.x, y = blockIdx.y * IBY + threadIdx.y;
+  const int tx = ceil_div(nx, IBX);
+  const int x = (int)(blockIdx.x % tx) * IBX + threadIdx.x, y = (int)(blockIdx.x / tx) * IBY + threadIdx.y;
   if (x >= nx || y >= ny) return;
   dst[(long long)y * nx + x] = (double)src[(long long)y * pitch + x] + add;
 }
 
 __global__ void k_pitch_T(const double *__restrict__ T, int nx, int ny, int pitch, double T_ref,
                           float *__restrict__ dst) {
-  const int x = blockIdx.x * IBX + threadIdx.x, y = blockIdx.y * IBY + threadIdx.y;
+  const int tx = ceil_div(pitch, IBX);
+  const int x = (int)(blockIdx.x % tx) * IBX + threadIdx.x, y = (int)(blockIdx.x / tx) * IBY + threadIdx.y;
   if (x >= pitch || y >= ny) return;
   double v = 0.0;
   if (x < nx) v = T[(long long)y * nx + x] - T_ref;
@@ -115,21 +118,27 @@ __global__ void k_pitch_T(const double *__restrict__ T, int nx, int ny, int pitc
 
 cudaError_t launch_unpitch(const float *src, int nx, int ny, int pitch, double add, double *dst,
                            cudaStream_t s) {
-  dim3 grid((nx + IBX - 1) / IBX, (ny + IBY - 1) / IBY);
+  dim3 grid;
+  cudaError_t e = tile_grid(ceil_div(nx, IBX), ceil_div(ny, IBY), grid);
+  if (e != cudaSuccess) return e;
   k_unpitch<<<grid, dim3(IBX, IBY), 0, s>>>(src, nx, ny, pitch, add, dst);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pitch_T(const double *T, int nx, int ny, int pitch, double T_ref, float *dst,
                            cudaStream_t s) {
-  dim3 grid((pitch + IBX - 1) / IBX, (ny + IBY - 1) / IBY);
+  dim3 grid;
+  cudaError_t e = tile_grid(ceil_div(pitch, IBX), ceil_div(ny, IBY), grid);
+  if (e != cudaSuccess) return e;
   k_pitch_T<<<grid, dim3(IBX, IBY), 0, s>>>(T, nx, ny, pitch, T_ref, dst);
   return cudaGetLastError();
 }
 
 cudaError_t launch_init(const DevParams &p, int storage, const double *rho0, void *gout,
                         cudaStream_t s) {
-  dim3 grid((p.nx + IBX - 1) / IBX, (p.ny + IBY - 1) / IBY);
+  dim3 grid;
+  cudaError_t e = tile_grid(ceil_div(p.nx, IBX), ceil_div(p.ny, IBY), grid);
+  if (e != cudaSuccess) return e;
   switch (storage) {
     case STORAGE_BF16:
       k_init<StoreBF16><<<grid, dim3(IBX, IBY), 0, s>>>(p, rho0, static_cast<__nv_bfloat16 *>(gout));

@@ -120,6 +120,16 @@ struct StepScalars {
   float rho_in; // inlet density of time t (pressure inlet)
 };
 
+// 2D tilings launched as 1D grids: a grid's y dimension stops at 65535 blocks and a
+// lattice may have 2^20 rows.  Block b covers tile (b % tiles_x, b / tiles_x).
+__host__ __device__ constexpr int ceil_div(int a, int b) { return (a + b - 1) / b; }
+inline cudaError_t tile_grid(int tiles_x, int tiles_y, dim3 &grid) {
+  const long long n = (long long)tiles_x * tiles_y;
+  if (n < 1 || n > 2147483647LL) return cudaErrorInvalidConfiguration;
+  grid = dim3((unsigned)n);
+  return cudaSuccess;
+}
+
 __device__ __forceinline__ int wrapi(int v, int n) {
   v = v < 0 ? v + n : v;
   return v >= n ? v - n : v;

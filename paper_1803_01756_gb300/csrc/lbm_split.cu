@@ -19,7 +19,8 @@ __global__ void __launch_bounds__(BX *BY)
     k_density_psi(DevParams p, const typename S::T *__restrict__ gs, const float *__restrict__ Tdev,
                   float *__restrict__ rho_o, float *__restrict__ psi_o, unsigned *status,
                   StepScalars sc) {
-  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  const int tx = ceil_div(p.nx, BX);
+  const int x = (int)(blockIdx.x % tx) * BX + threadIdx.x, y = (int)(blockIdx.x / tx) * BY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   float g[9];
   pull<S>(p, gs, x, y, sc, g);
@@ -45,7 +46,8 @@ __global__ void __launch_bounds__(BX *BY)
               const float *__restrict__ Tdev, const float *__restrict__ psi,
               float *__restrict__ ux_o, float *__restrict__ uy_o, unsigned *status,
               StepScalars sc) {
-  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  const int tx = ceil_div(p.nx, BX);
+  const int x = (int)(blockIdx.x % tx) * BX + threadIdx.x, y = (int)(blockIdx.x / tx) * BY + threadIdx.y;
   if (x >= p.nx || y >= p.ny) return;
   float g[9];
   pull<S>(p, gs, x, y, sc, g);
@@ -115,7 +117,8 @@ __global__ void __launch_bounds__(ETHREADS)
   __shared__ short sred[ERN];
   __shared__ unsigned char skind[ERN];
 
-  const int x0 = blockIdx.x * ETX - EH, y0 = blockIdx.y * ETY - EH;
+  const int tx = ceil_div(p.nx, ETX);
+  const int x0 = (int)(blockIdx.x % tx) * ETX - EH, y0 = (int)(blockIdx.x / tx) * ETY - EH;
   const int tid = threadIdx.x;
 
   for (int i = tid; i < ERN; i += ETHREADS) {
@@ -258,7 +261,9 @@ __global__ void __launch_bounds__(ETHREADS)
 template <class S>
 cudaError_t density_psi_t(const DevParams &p, const void *gs, const float *Tdev, float *rho,
                           float *psi, unsigned *status, StepScalars sc, cudaStream_t s) {
-  dim3 grid((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY);
+  dim3 grid;
+  cudaError_t e = tile_grid(ceil_div(p.nx, BX), ceil_div(p.ny, BY), grid);
+  if (e != cudaSuccess) return e;
   k_density_psi<S><<<grid, dim3(BX, BY), 0, s>>>(p, static_cast<const typename S::T *>(gs), Tdev,
                                                  rho, psi, status, sc);
   return cudaGetLastError();
@@ -269,7 +274,9 @@ cudaError_t collide_t(const DevParams &p, const void *gs, void *gout, const floa
                       const float *psi, float *ux, float *uy, unsigned *status, StepScalars sc,
                       bool write_populations, cudaStream_t s) {
   using T = typename S::T;
-  dim3 grid((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY);
+  dim3 grid;
+  cudaError_t e = tile_grid(ceil_div(p.nx, BX), ceil_div(p.ny, BY), grid);
+  if (e != cudaSuccess) return e;
   const T *in = static_cast<const T *>(gs);
   T *out = static_cast<T *>(gout);
   if (write_populations)
@@ -308,7 +315,9 @@ cudaError_t launch_collide(const DevParams &p, int storage, const void *gs, void
 cudaError_t launch_energy(const DevParams &p, const float *Tin, float *Tout, const float *rho,
                           const float *ux, const float *uy, unsigned *status, StepScalars sc,
                           cudaStream_t s) {
-  dim3 grid((p.nx + ETX - 1) / ETX, (p.ny + ETY - 1) / ETY);
+  dim3 grid;
+  cudaError_t e = tile_grid(ceil_div(p.nx, ETX), ceil_div(p.ny, ETY), grid);
+  if (e != cudaSuccess) return e;
   k_energy<<<grid, ETHREADS, 0, s>>>(p, Tin, Tout, rho, ux, uy, status, sc);
   return cudaGetLastError();
 }

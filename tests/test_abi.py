@@ -79,3 +79,18 @@ def test_host_only_entry_points(lib):
     # invalid sizes are rejected before any device call
     assert L.lbm_create(0, 10, ctypes.byref(p), ctypes.byref(h)) == -1
     L.lbm_destroy(None)
+
+
+@pytest.mark.parametrize("nx,ny,over", [
+    (0, 8, dict()), (8, 0, dict()), ((1 << 20) + 1, 4, dict()), (4, (1 << 20) + 1, dict()),
+    (1, 8, dict()),                 # an open x end needs two columns
+    (16, 8, dict(x_bc=7)), (16, 8, dict(y_bc=3)), (16, 8, dict(tau_g=0.5)),
+    (16, 8, dict(s_q=2.0)), (16, 8, dict(x_bc=2, p_amp_frac=1.0)),
+])
+def test_invalid_arguments_are_rejected(lib, nx, ny, over):
+    """lbm_create validates sizes and parameters before any device call (no GPU needed)."""
+    from paper_1803_01756_gb300 import inputs
+    from paper_1803_01756_gb300.lattice import Lattice, LbmError
+    with pytest.raises(LbmError) as ei:
+        Lattice(nx, ny, inputs.base_params(**over))
+    assert ei.value.code == -1  # LBM_ERR_ARG

@@ -223,6 +223,18 @@ def test_beyond_l2_channel_16384x2048():
     assert max(err.values()) <= TOL, err
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("nx,ny,over", [(1 << 20, 1, dict()), (1, 1 << 20, dict(x_bc=0))])
+def test_largest_extents(nx, ny, over, kernel):
+    """The largest lattice extent the library accepts (2^20 nodes) along x and along y,
+    against the oracle after 3 updates."""
+    p = inputs.base_params(**over)
+    rho0 = inputs.noisy_density(nx, ny, inputs.RHO_V_086, 0.01, seed=13)
+    gpu, ref = run_both(nx, ny, p, rho0, 3, kernel)
+    err = rel_errors(gpu, ref)
+    assert max(err.values()) <= TOL, err
+
+
 def test_mass_reduction_matches_oracle():
     nx, ny = 40, 24
     p = inputs.base_params(x_bc=0)
