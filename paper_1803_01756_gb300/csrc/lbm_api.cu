@@ -424,7 +424,8 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
     // LBM_FUSED_TILE="W,H" overrides the tiling (tuning experiments)
     if (const char *env = std::getenv("LBM_FUSED_TILE")) {
       int W = 0, H = 0;
-      if (std::sscanf(env, "%d,%d", &W, &H) == 2 && W >= 1 && W <= 118 && H >= 1)
+      if (std::sscanf(env, "%d,%d", &W, &H) == 2 && W >= 1 && W <= lbm::fused_max_width() &&
+          H >= 1 && (ny + H - 1) / H <= 65535 && lbm::fused_supported(h->dp))
         h->fused = lbm::FusedTiling{W, H};
     }
     if (h->fused.W > 0) {
