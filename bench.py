@@ -312,6 +312,71 @@ def our_arm(args, world, rank, local, dist):
     print(json.dumps(line), flush=True)
 
 
+def batch_channels(n: int = 96, seed: int = 3):
+    """Seeded batch mix: n channels with length U[256, 2048], width U[32, 256], wall
+    strength U[-1.2, -1.1] and inlet period U[2000, 20000] (15.8 M nodes for n = 96)."""
+    u = inputs.uniform01(4 * n, seed).reshape(n, 4)
+    out = []
+    for k in range(n):
+        nx, ny = int(256 + u[k, 0] * 1792), int(32 + u[k, 1] * 224)
+        p = inputs.base_params(Gw=-1.2 + 0.1 * u[k, 2], u_amp=0.02,
+                               u_period=float(2000 + int(18000 * u[k, 3])))
+        out.append((nx, ny, p, inputs.noisy_density(nx, ny, inputs.RHO_V_086, 0.01, nx)))
+    return out
+
+
+def batch_arm(args):
+    """MLUPS of one persistent launch per update over the batch mix, against the same
+    lattices advanced one after another with lbm_step."""
+    import torch
+    from paper_1803_01756_gb300 import lattice as L
+    torch.cuda.set_device(0)
+    specs = batch_channels()
+    lats = []
+    for nx, ny, p, rho0 in specs:
+        lat = L.Lattice(nx, ny, p, kernel=L.KERNEL_FUSED)
+        lat.write_fields(rho0)
+        lats.append(lat)
+    cells = sum(nx * ny for nx, ny, _, _ in specs)
+    stream = torch.cuda.current_stream()
+    b = L.Batch(lats)
+    info = b.info()
+    b.step(args.warmup, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(args.steps, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    b.close()
+    seq_steps = max(1, min(args.steps, 200))
+    for lat in lats:
+        lat.step(2, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for lat in lats:
+        lat.step(seq_steps, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    status = 0
+    for lat in lats:
+        status |= lat.status()
+        lat.close()
+    line = {
+        "metric": "lattice updates per second (MLUPS), batched channels", "value":
+        cells * args.steps / ms / 1e3, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch: {len(specs)} channels 256-2048 x 32-256, {cells} nodes",
+                   "tiles": info["tiles"], "tile_rows": info["tile_rows"], "grid": info["grid"]},
+        "sequential_mlups": cells * seq_steps / seq_ms / 1e3, "gpu_launches": args.steps,
+        "status_bits": status,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def serving_jobs(n: int, steps: int, seed: int = 4):
     """Seeded job stream: 90 % channels with length U[256, 2048], width U[32, 256],
     wall strength U[-1.25, -1.08] (contact angles ~40-130 degrees), inlet period
@@ -413,8 +478,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-inner", type=int, default=100)
     ap.add_argument("--e2e-reps", type=int, default=5)
-    ap.add_argument("--mode", default="lattice", choices=["lattice", "serve"],
-                    help="lattice: MLUPS of one channel; serve: the job server")
+    ap.add_argument("--mode", default="lattice", choices=["lattice", "batch", "serve"],
+                    help="lattice: MLUPS of one channel; batch: one launch per update over 96 "
+                         "channels; serve: the job server")
     ap.add_argument("--jobs", type=int, default=160)
     ap.add_argument("--job-steps", type=int, default=2000)
     ap.add_argument("--max-active", type=int, default=64)
@@ -427,6 +493,9 @@ def main():
     try:
         if args.impl == "reference":
             reference_arm(args, world, rank)
+        elif args.mode == "batch":
+            if rank == 0:
+                batch_arm(args)
         elif args.mode == "serve":
             if rank == 0:
                 serving_arm(args)
