@@ -44,6 +44,12 @@ L2_BYTES = 129e6
 FUSED_F32_4096x512_DRAM_BYTES = 109.544192e6 + 41.230080e6
 
 
+# --physics: which parts of the update run (the energy equation of Eqs. 16-18 and the
+# pseudopotential forces of Eqs. 9-14 are separate switches of the library)
+PHYSICS = {"full": {}, "no-thermal": {"thermal": 0}, "no-multiphase": {"multiphase": 0},
+           "plain": {"thermal": 0, "multiphase": 0}}
+
+
 def env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -191,6 +197,8 @@ def our_arm(args, world, rank, local, dist):
     assert torch.cuda.is_available(), "bench.py needs a CUDA device"
     torch.cuda.set_device(local)
     w = inputs.workload(args.workload)
+    # parts of the update switched off (to see what each part costs); the default is all
+    w["params"] = dict(w["params"], **PHYSICS[args.physics])
     nx, ny = w["nx"], w["ny"]
     kernel = {"auto": L.KERNEL_AUTO, "split": L.KERNEL_SPLIT, "fused": L.KERNEL_FUSED}[args.kernel]
     storage = {"f32": 0, "bf16": 1, "f16": 2}[args.storage]
@@ -248,7 +256,7 @@ def our_arm(args, world, rank, local, dist):
     per_cell = bytes_cell if top_name == "k_fused_step" else SPLIT_KERNEL_BYTES[top_name]
     traffic = args.traffic
     if (traffic is None and top_name == "k_fused_step" and args.storage == "f32"
-            and args.workload == "channel_4096x512"):
+            and args.workload == "channel_4096x512" and args.physics == "full"):
         traffic = FUSED_F32_4096x512_DRAM_BYTES
     bytes_per_launch = per_cell * cells
     achieved = bytes_per_launch / (top_ms / top_n / 1e3) / 1e9
@@ -301,6 +309,7 @@ def our_arm(args, world, rank, local, dist):
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "nx": nx, "ny": ny, "storage": args.storage,
+                   "physics": args.physics,
                    "kernel": {1: "split", 2: "fused"}[info["kernel"]],
                    "parallelism": f"replicas x{world}",
                    "l2": f"state {info['device_bytes'] / 1e6:.0f} MB > L2 129 MB; no flush",
@@ -471,6 +480,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="channel_4096x512", choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
+    ap.add_argument("--physics", default="full", choices=sorted(PHYSICS),
+                    help="full update, or without the energy equation / the pseudopotential")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="population storage (FP32 arithmetic in every case)")
     ap.add_argument("--cpu-steps", type=int, default=10)
