@@ -102,8 +102,9 @@ typedef struct lbm_info {
 
 /* Create a lattice of nx * ny nodes with parameters *p.  Allocates all device
    memory of the handle on the current device; the populations start at the
-   equilibrium of rho_g at rest and T = T0.  LBM_ERR_ARG for nx, ny < 1, nx < 2
-   with open x ends, or invalid parameters; LBM_ERR_OOM if allocation fails. */
+   equilibrium of rho_g at rest and T = T0.  LBM_ERR_ARG for nx or ny outside
+   [1, 2^20], nx < 2 with open x ends, or invalid parameters (checked before any
+   device call); LBM_ERR_OOM if allocation fails. */
 int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out);
 
 /* Set the state at the current time from host fields: populations f = f^eq(rho, u = 0)
