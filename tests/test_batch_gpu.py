@@ -121,3 +121,33 @@ def test_default_tile_height_follows_the_batch_size():
     b.close()
     for lat in small + [big]:
         lat.close()
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_batch_against_the_oracle(storage):
+    """Each lattice of a batch of uneven channels (default tile height) against the FP64
+    oracle after 150 updates: within 1e-5 with FP32 storage, within the FP16 bounds of
+    the precision tests with FP16 storage."""
+    import oracle
+    from paper_1803_01756_gb300.lattice import Batch, Lattice
+    specs = channel_set(5, seed=60)
+    lats = []
+    for nx, ny, p, rho0 in specs:
+        lat = Lattice(nx, ny, p, kernel=2, storage=storage)
+        lat.write_fields(rho0)
+        lats.append(lat)
+    b = Batch(lats)
+    b.step(150)
+    b.close()
+    tol = {"rho": 1e-5, "u": 1e-5, "T": 1e-5} if storage == 0 else \
+        {"rho": 2e-3, "u": 1.5e-2, "T": 5e-4}
+    for lat, (nx, ny, p, rho0) in zip(lats, specs):
+        rho, ux, uy, T = lat.read_fields()
+        o = oracle.Oracle(nx, ny, p)
+        o.set_fields(rho0)
+        o.step(150)
+        rr, rux, ruy, rT = o.fields()
+        assert np.abs(rho - rr).max() <= tol["rho"] * np.abs(rr).max()
+        assert np.hypot(ux - rux, uy - ruy).max() <= tol["u"] * max(np.hypot(rux, ruy).max(), 1e-2)
+        assert np.abs(T - rT).max() <= tol["T"] * np.abs(rT).max()
+        lat.close()
