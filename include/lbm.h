@@ -98,6 +98,8 @@ typedef struct lbm_info {
   double T_ref, rho_ref;      /* deviation references of the stored T and populations */
   size_t device_bytes;        /* device memory held by the handle */
   int kernel;                 /* kernel path in use (LBM_KERNEL_SPLIT or _FUSED) */
+  int tile_cols, tile_rows;   /* fused kernel: most output columns and rows of one CTA's tile
+                                 (0 on the split path) */
 } lbm_info_t;
 
 /* Create a lattice of nx * ny nodes with parameters *p.  Allocates all device
@@ -116,8 +118,18 @@ int lbm_write_fields(lbm_h h, const double *rho, const double *T, void *stream);
 /* Advance nsteps lattice updates (Eqs. 1-18 per update): pull-streaming with bounce-back
    and Zou-He rules, density, pseudopotential (Eqs. 10-11), forces (Eqs. 9, 14, 15),
    velocity (Eq. 13), moment-space collision with Li forcing (Eqs. 6-8) and the RK4
-   temperature update (Eqs. 16-18).  Asynchronous: only enqueues launches on the stream. */
+   temperature update (Eqs. 16-18).  Asynchronous: enqueues work on the stream; on the
+   fused path the updates go in chunks of 16, each preceded by a 192-byte copy of its
+   boundary scalars from pinned host memory, and the host may wait for the copy of the
+   chunk before last.  Calls on different streams must be ordered by the caller (they
+   share the lattice state). */
 int lbm_step(lbm_h h, long nsteps, void *stream);
+
+/* enable != 0 (the default): lbm_step replays each full chunk of 16 fused updates from a
+   CUDA graph captured on first use (one per buffer parity); 0: one launch per update.
+   Per-launch timing (lbm_timing_enable) always launches one by one; the split path never
+   uses graphs.  Results are identical either way. */
+int lbm_set_graph(lbm_h h, int enable);
 
 /* Copy the fields of the current time t to host arrays (any may be NULL): rho = sum f,
    u = (sum e f + F/2) / rho (Eq. 13, force of time t), T absolute.  Synchronises the

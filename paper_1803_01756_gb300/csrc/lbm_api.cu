@@ -1,4 +1,5 @@
 // Host runtime and C ABI (include/lbm.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -296,42 +297,128 @@ int compute_rho_psi(lbm_lattice *h, cudaStream_t s) {
                                            h->rho, h->psi, h->status, sc, s));
 }
 
-int one_update(lbm_lattice *h, cudaStream_t s) {
+void advance(lbm_lattice *h) {
+  h->cur ^= 1;
+  if (h->dp.thermal) h->tcur ^= 1;
+  h->t += 1;
+}
+
+// one update through the split path (three launches)
+int split_update(lbm_lattice *h, cudaStream_t s) {
   StepScalars sc = scalars_at(h, h->t);
   const DevParams &d = h->dp;
-  int rc;
-  if (h->kernel == LBM_KERNEL_FUSED) {
-    rc = timed(h, KN_FUSED, s, [&] {
-      return lbm::launch_fused(d, h->p.storage, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur],
-                               h->T[1 - h->tcur], h->status, sc, h->fused, s);
+  int rc = timed(h, KN_DENSITY, s, [&] {
+    return lbm::launch_density_psi(d, h->p.storage, h->g[h->cur], h->T[h->tcur], h->rho, h->psi,
+                                   h->status, sc, s);
+  });
+  if (rc) return rc;
+  rc = timed(h, KN_COLLIDE, s, [&] {
+    return lbm::launch_collide(d, h->p.storage, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur],
+                               h->psi, h->ux, h->uy, h->status, sc, true, s);
+  });
+  if (rc) return rc;
+  if (d.thermal) {
+    rc = timed(h, KN_ENERGY, s, [&] {
+      return lbm::launch_energy(d, h->T[h->tcur], h->T[1 - h->tcur], h->rho, h->ux, h->uy,
+                                h->status, sc, s);
     });
     if (rc) return rc;
-  } else {
-    rc = timed(h, KN_DENSITY, s, [&] {
-      return lbm::launch_density_psi(d, h->p.storage, h->g[h->cur], h->T[h->tcur], h->rho,
-                                     h->psi, h->status, sc, s);
-    });
-    if (rc) return rc;
-    rc = timed(h, KN_COLLIDE, s, [&] {
-      return lbm::launch_collide(d, h->p.storage, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur],
-                                 h->psi, h->ux, h->uy, h->status, sc, true, s);
-    });
-    if (rc) return rc;
-    if (d.thermal) {
-      rc = timed(h, KN_ENERGY, s, [&] {
-        return lbm::launch_energy(d, h->T[h->tcur], h->T[1 - h->tcur], h->rho, h->ux, h->uy,
-                                  h->status, sc, s);
-      });
-      if (rc) return rc;
-    }
   }
-  h->cur ^= 1;
-  if (d.thermal) h->tcur ^= 1;
-  h->t += 1;
+  advance(h);
+  return LBM_OK;
+}
+
+// the fused launch of the current update, with the scalars of slot k of d_sc
+cudaError_t fused_launch(lbm_lattice *h, int k, cudaStream_t s) {
+  return lbm::launch_fused(h->dp, h->p.storage, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur],
+                           h->T[1 - h->tcur], h->status, h->d_sc + k, h->fused, s);
+}
+
+// Scalars of updates t .. t + m - 1 into d_sc, through the staging buffer whose previous
+// copy has completed.
+int stage_scalars(lbm_lattice *h, int m, cudaStream_t s) {
+  const int buf = h->sc_buf;
+  if (h->sc_used[buf]) LBM_CUDA(cudaEventSynchronize(h->sc_ev[buf]));
+  for (int k = 0; k < m; k++) h->h_sc[buf][k] = scalars_at(h, h->t + k);
+  LBM_CUDA(cudaMemcpyAsync(h->d_sc, h->h_sc[buf], sizeof(StepScalars) * m,
+                           cudaMemcpyHostToDevice, s));
+  LBM_CUDA(cudaEventRecord(h->sc_ev[buf], s));
+  h->sc_used[buf] = true;
+  h->sc_buf ^= 1;
+  return LBM_OK;
+}
+
+void drop_graphs(lbm_lattice *h) {
+  for (int c = 0; c < 2; c++)
+    for (int k = 0; k < 2; k++) {
+      if (h->gexec[c][k]) cudaGraphExecDestroy(h->gexec[c][k]);
+      if (h->graph[c][k]) cudaGraphDestroy(h->graph[c][k]);
+      h->gexec[c][k] = nullptr;
+      h->graph[c][k] = nullptr;
+    }
+}
+
+// Capture the kChunk launches of a chunk that starts at the current buffer parity.
+int capture_chunk(lbm_lattice *h) {
+  const int c0 = h->cur, t0 = h->tcur;
+  LBM_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < lbm_lattice::kChunk; k++) {
+    if (e == cudaSuccess) e = fused_launch(h, k, h->cap_stream);
+    h->cur ^= 1;
+    if (h->dp.thermal) h->tcur ^= 1;
+  }
+  h->cur = c0;
+  h->tcur = t0;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
+  if (e == cudaSuccess) e = ee;
+  cudaGraphExec_t x = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(e);
+  }
+  h->graph[c0][t0] = g;
+  h->gexec[c0][t0] = x;
+  return LBM_OK;
+}
+
+// nsteps fused updates: chunks of kChunk, each a graph replay when graphs are on and
+// per-launch timing is off, else one launch per update
+int fused_steps(lbm_lattice *h, long nsteps, cudaStream_t s) {
+  const int C = lbm_lattice::kChunk;
+  for (long done = 0; done < nsteps;) {
+    const int m = (int)std::min<long>(C, nsteps - done);
+    int rc = stage_scalars(h, m, s);
+    if (rc) return rc;
+    if (m == C && h->use_graph && !h->timing) {
+      if (!h->gexec[h->cur][h->tcur]) {
+        rc = capture_chunk(h);
+        if (rc) return rc;
+      }
+      LBM_CUDA(cudaGraphLaunch(h->gexec[h->cur][h->tcur], s));
+      h->t += C;  // an even chunk ends at the parity it started from
+    } else {
+      for (int k = 0; k < m; k++) {
+        rc = timed(h, KN_FUSED, s, [&] { return fused_launch(h, k, s); });
+        if (rc) return rc;
+        advance(h);
+      }
+    }
+    done += m;
+  }
   return LBM_OK;
 }
 
 void free_all(lbm_lattice *h) {
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int k = 0; k < 2; k++) {
+    if (h->h_sc[k]) cudaFreeHost(h->h_sc[k]);
+    if (h->sc_ev[k]) cudaEventDestroy(h->sc_ev[k]);
+  }
+  cudaFree(h->d_sc);
   cudaFree(h->g[0]);
   cudaFree(h->g[1]);
   cudaFree(h->T[0]);
@@ -454,6 +541,15 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
   if (e == cudaSuccess) e = dalloc(h, &h->sums, 2);
   if (e == cudaSuccess) e = dalloc(h, &h->rho0, (size_t)nx * ny);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_sums, 2 * sizeof(double));
+  if (h->kernel == LBM_KERNEL_FUSED) {
+    const int C = lbm_lattice::kChunk;
+    if (e == cudaSuccess) e = dalloc(h, &h->d_sc, C);
+    for (int k = 0; k < 2 && e == cudaSuccess; k++)
+      e = cudaMallocHost((void **)&h->h_sc[k], C * sizeof(StepScalars));
+    for (int k = 0; k < 2 && e == cudaSuccess; k++)
+      e = cudaEventCreateWithFlags(&h->sc_ev[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  }
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(unsigned));
   // padding columns stay zero forever
   for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMemset(h->g[k], 0, 9 * plane * (size_t)h->esize);
@@ -493,9 +589,20 @@ int lbm_step(lbm_h h, long nsteps, void *stream) {
   if (!h || nsteps < 0) return LBM_ERR_ARG;
   LBM_CUDA(cudaSetDevice(h->device));
   cudaStream_t s = (cudaStream_t)stream;
+  if (h->kernel == LBM_KERNEL_FUSED) return fused_steps(h, nsteps, s);
   for (long k = 0; k < nsteps; k++) {
-    int rc = one_update(h, s);
+    int rc = split_update(h, s);
     if (rc) return rc;
+  }
+  return LBM_OK;
+}
+
+int lbm_set_graph(lbm_h h, int enable) {
+  if (!h) return LBM_ERR_ARG;
+  h->use_graph = enable != 0;
+  if (!h->use_graph) {
+    LBM_CUDA(cudaSetDevice(h->device));
+    drop_graphs(h);
   }
   return LBM_OK;
 }
@@ -620,6 +727,9 @@ int lbm_info(lbm_h h, lbm_info_t *info) {
   info->rho_ref = h->rho_ref;
   info->device_bytes = h->device_bytes;
   info->kernel = h->kernel;
+  const bool fused = h->kernel == LBM_KERNEL_FUSED;
+  info->tile_cols = fused ? h->fused.W : 0;
+  info->tile_rows = fused ? h->fused.H : 0;
   return LBM_OK;
 }
 

@@ -10,7 +10,8 @@ template <bool YW, bool XO, bool TH, bool MP, class ST>
 __global__ void __launch_bounds__(FNT, LBM_FUSED_MIN_CTAS)
     k_fused_step(DevParams p, const typename ST::T *__restrict__ gs,
                  typename ST::T *__restrict__ gout, const float *__restrict__ Tin,
-                 float *__restrict__ Tout, unsigned *status, StepScalars sc) {
+                 float *__restrict__ Tout, unsigned *status,
+                 const StepScalars *__restrict__ sc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
   // strips and row chunks of nearly equal size (they differ by at most one column or row)
@@ -18,7 +19,12 @@ __global__ void __launch_bounds__(FNT, LBM_FUSED_MIN_CTAS)
   const int X1 = (int)(((long long)(blockIdx.x + 1) * p.nx) / gridDim.x);
   const int Y0 = (int)(((long long)blockIdx.y * p.ny) / gridDim.y);
   const int ye = (int)(((long long)(blockIdx.y + 1) * p.ny) / gridDim.y);
-  fused_tile<YW, XO, TH, MP, ST, 2>(p, p, gs, gout, Tin, Tout, status, sc, X0, X1 - X0, Y0, ye, S);
+  // the update's boundary scalars, read where used (registers are at the launch bound)
+  __shared__ StepScalars ssc;
+  if (threadIdx.x == 0) ssc = *sc;
+  __syncthreads();
+  fused_tile<YW, XO, TH, MP, ST, 2>(p, p, gs, gout, Tin, Tout, status, ssc, X0, X1 - X0, Y0, ye,
+                                    S);
 }
 
 }  // namespace
@@ -32,7 +38,7 @@ namespace {
 
 template <class ST>
 using FusedFn = void (*)(DevParams, const typename ST::T *, typename ST::T *, const float *,
-                         float *, unsigned *, StepScalars);
+                         float *, unsigned *, const StepScalars *);
 
 template <class ST>
 FusedFn<ST> fused_variant(const DevParams &p) {
@@ -61,7 +67,7 @@ cudaError_t prepare(const DevParams &p, int *occ) {
 
 template <class ST>
 cudaError_t launch_t(const DevParams &p, const void *gs, void *gout, const float *Tin, float *Tout,
-                     unsigned *status, StepScalars sc, FusedTiling tl, cudaStream_t s) {
+                     unsigned *status, const StepScalars *sc, FusedTiling tl, cudaStream_t s) {
   // ceil(nx / W) strips of at most W columns and ceil(ny / H) chunks of at most H rows
   dim3 grid((p.nx + tl.W - 1) / tl.W, (p.ny + tl.H - 1) / tl.H);
   fused_variant<ST>(p)<<<grid, FNT, sizeof(FusedSmem), s>>>(
@@ -82,21 +88,40 @@ FusedTiling fused_tiling(const DevParams &p, int storage, int device) {
                   : storage == STORAGE_F16 ? prepare<StoreF16>(p, &occ)
                                            : prepare<StoreF32>(p, &occ);
   if (e != cudaSuccess || occ < 1) return best;
-  // Widest strips (fewest halo columns) and one wave of resident CTAs: measured on
-  // the 4096 x 512 channel, equal-work tilings with narrower strips or two waves
-  // were 2-35 % slower than this.
+  // Widest strips (fewest halo columns), then the row-chunk height H with the shortest
+  // estimated launch time over one wave of resident CTAs.  Every CTA sweeps H + 15 row
+  // steps, and a row step takes longer the more CTAs share the SM: one CTA alone is bound
+  // by the latency of the row step, four share the SM's issue slots.  kStep is the
+  // measured time of one row step with k CTAs per SM, relative (200 x 50, 1024 x 128 and
+  // 4096 x 512 channels, FP32); equal-work tilings with narrower strips or two waves were
+  // 2-35 % slower on 4096 x 512.  A small lattice thus gets short chunks spread over
+  // idle SMs (1 row on 200 x 50, 2x the rate of 16-row chunks), a large one one wave
+  // of tall chunks.
+  static const double kStep[5] = {0.0, 0.85, 0.97, 1.42, 1.64};
   const long long slots = (long long)sms * occ;
   const int strips = (p.nx + FW - 1) / FW;
-  long long chunks = slots / strips;
-  if (chunks < 1) chunks = 1;
-  int H = (int)((p.ny + chunks - 1) / chunks);
-  if (H < 16) H = 16;
+  long long max_chunks = slots / strips;
+  if (max_chunks < 1) max_chunks = 1;
+  if (max_chunks > p.ny) max_chunks = p.ny;
+  int H = p.ny;
+  double best_cost = -1.0;
+  for (long long c = 1; c <= max_chunks; c++) {
+    const int h = (int)((p.ny + c - 1) / c);
+    const long long tiles = (long long)strips * ((p.ny + h - 1) / h);
+    const long long k = (tiles + sms - 1) / sms;  // CTAs per SM
+    const double step = k <= 4 ? kStep[k] : kStep[4] * (double)k / 4.0;
+    const double cost = (h + 15) * step;
+    if (best_cost < 0.0 || cost < best_cost) {  // ties keep the taller chunk
+      best_cost = cost;
+      H = h;
+    }
+  }
   best = FusedTiling{FW, H};
   return best;
 }
 
 cudaError_t launch_fused(const DevParams &p, int storage, const void *gs, void *gout,
-                         const float *Tin, float *Tout, unsigned *status, StepScalars sc,
+                         const float *Tin, float *Tout, unsigned *status, const StepScalars *sc,
                          FusedTiling tl, cudaStream_t s) {
   if (tl.H < 1 || tl.W < 1 || tl.W > FW) return cudaErrorInvalidValue;
   switch (storage) {

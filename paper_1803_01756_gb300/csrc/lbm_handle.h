@@ -41,6 +41,20 @@ struct lbm_lattice {
   double *rho0 = nullptr;  // device staging (nx * ny doubles) for the field copies in and out
   double *host_sums = nullptr;  // pinned, 2 doubles
   size_t device_bytes = 0;
+  // Fused updates run in chunks of kChunk: the chunk's boundary scalars (one StepScalars per
+  // update) go from a pinned staging buffer (two, alternating) to d_sc, then a full chunk
+  // replays a captured CUDA graph of kChunk launches when graphs are on.  A chunk has an
+  // even length, so it starts and ends at the same buffer parity: gexec[cur][tcur].
+  static constexpr int kChunk = 16;
+  lbm::StepScalars *d_sc = nullptr;
+  lbm::StepScalars *h_sc[2] = {nullptr, nullptr};
+  cudaEvent_t sc_ev[2] = {nullptr, nullptr};
+  bool sc_used[2] = {false, false};
+  int sc_buf = 0;
+  bool use_graph = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   // timing
   bool timing = false;
   std::vector<lbm_host::TimedLaunch> pending;

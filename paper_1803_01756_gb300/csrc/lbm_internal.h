@@ -34,13 +34,13 @@ struct BatchChannel {
   int tile_begin;    // index of its first tile in the work-list
 };
 
-// fused path: one launch per update
+// fused path: one launch per update; sc points to the update's scalars in device memory
 struct FusedTiling {
   int W;  // output columns per CTA (at most 118)
   int H;  // output rows per CTA
 };
 cudaError_t launch_fused(const DevParams &p, int storage, const void *gs, void *gout,
-                         const float *Tin, float *Tout, unsigned *status, StepScalars sc,
+                         const float *Tin, float *Tout, unsigned *status, const StepScalars *sc,
                          FusedTiling tiling, cudaStream_t s);
 bool fused_supported(const DevParams &p);
 // tiling for one wave of resident CTAs on this device ({0, 0} on failure); also sets

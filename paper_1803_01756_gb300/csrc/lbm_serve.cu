@@ -58,13 +58,14 @@ struct lbm_server {
 namespace {
 
 // device bytes lbm_create allocates for a lattice (populations x2, T x2, four scratch
-// planes, reduction partials, staging); used for admission before allocating
+// planes, reduction partials, staging, the boundary scalars of one graph chunk); used for
+// admission before allocating
 size_t footprint_of(int nx, int ny, int storage) {
   const size_t pitch = (size_t)((nx + 31) / 32 * 32);
   const size_t plane = pitch * (size_t)ny;
   const size_t es = storage == LBM_STORAGE_F32 ? 4 : 2;
   return 2 * 9 * plane * es + 6 * plane * sizeof(float) + (size_t)nx * ny * sizeof(double) +
-         2 * 1216 * sizeof(double) + 64;
+         2 * 1216 * sizeof(double) + 64 + lbm_lattice::kChunk * sizeof(lbm::StepScalars);
 }
 
 void retire(lbm_server *s, const std::shared_ptr<Job> &j, int state) {

@@ -56,7 +56,8 @@ class LbmInfo(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pitch", ctypes.c_int),
                 ("t", ctypes.c_longlong), ("Tc", ctypes.c_double), ("T_ref", ctypes.c_double),
                 ("rho_ref", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("kernel", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("tile_cols", ctypes.c_int),
+                ("tile_rows", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -89,6 +90,7 @@ SIGNATURES = {
     "lbm_write_state": ([_vp, _vp, ctypes.c_size_t, _vp], ctypes.c_int),
     "lbm_info": ([_vp, ctypes.POINTER(LbmInfo)], ctypes.c_int),
     "lbm_timing_enable": ([_vp, ctypes.c_int], ctypes.c_int),
+    "lbm_set_graph": ([_vp, ctypes.c_int], ctypes.c_int),
     "lbm_timing_get": ([_vp, ctypes.POINTER(ctypes.c_char_p), _dp, ctypes.POINTER(ctypes.c_long),
                         ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp], ctypes.c_int),
     "lbm_destroy": ([_vp], None),
@@ -227,6 +229,9 @@ class Lattice:
 
     def step(self, nsteps: int = 1, stream=None):
         _check(self._lib.lbm_step(self._h, int(nsteps), _stream_ptr(stream)), "lbm_step")
+
+    def set_graph(self, enable: bool = True):
+        _check(self._lib.lbm_set_graph(self._h, int(bool(enable))), "lbm_set_graph")
 
     def read_fields(self, stream=None, check: bool = True):
         shp = (self.ny, self.nx)

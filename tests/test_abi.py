@@ -46,26 +46,41 @@ def test_binding_covers_every_declared_symbol():
     assert declared == bound, (declared ^ bound)
 
 
-def test_params_struct_layout_matches_header():
-    """The ctypes mirror lists the struct fields of include/lbm.h in order."""
-    from paper_1803_01756_gb300 import lattice
+def _header_fields(struct, typedef):
     text = open(os.path.join(ROOT, "include", "lbm.h")).read()
-    body = re.search(r"typedef struct lbm_params \{(.*?)\} lbm_params_t;", text, re.S).group(1)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (struct, typedef), text, re.S).group(1)
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = []
     for decl in body.split(";"):
-        decl = decl.strip()
+        decl = " ".join(decl.split())
         if not decl:
             continue
-        typ, rest = decl.split(None, 1)
+        typ, rest = re.match(r"(long long|size_t|double|int)\s+(.*)", decl).groups()
         for name in rest.split(","):
             fields.append((typ, name.strip()))
+    return fields
+
+
+CTYPE = {"double": ctypes.c_double, "int": ctypes.c_int, "long long": ctypes.c_longlong,
+         "size_t": ctypes.c_size_t}
+
+
+def test_params_struct_layout_matches_header():
+    """The ctypes mirror lists the struct fields of include/lbm.h in order."""
+    from paper_1803_01756_gb300 import lattice
+    fields = _header_fields("lbm_params", "lbm_params_t")
     mirror = [(f[0], f[1]) for f in lattice.LbmParams._fields_]
     assert len(fields) == len(mirror)
-    ctype = {"double": ctypes.c_double, "int": ctypes.c_int}
     for (typ, name), (mname, mtype) in zip(fields, mirror):
         assert (mname if mname != "lam" else "lambda") == name
-        assert mtype is ctype[typ]
+        assert mtype is CTYPE[typ]
+
+
+def test_info_struct_layout_matches_header():
+    from paper_1803_01756_gb300 import lattice
+    fields = _header_fields("lbm_info", "lbm_info_t")
+    mirror = [(f[0], f[1]) for f in lattice.LbmInfo._fields_]
+    assert [(n, CTYPE[t]) for t, n in fields] == mirror
 
 
 def test_host_only_entry_points(lib):

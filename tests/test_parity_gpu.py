@@ -310,3 +310,72 @@ def test_runs_on_a_side_stream():
     fb = b.read_fields()
     for x, y in zip(fa, fb):
         assert np.array_equal(x, y)
+
+
+def test_default_tiling_follows_the_lattice_size():
+    """The fused kernel's row-chunk height: short chunks spread a small lattice over
+    the SMs (each CTA sweeps its rows plus 15, one row step at a time), a large one gets
+    one wave of tall chunks (152 SMs with 4 resident CTAs each)."""
+    import torch
+    from paper_1803_01756_gb300.lattice import Lattice, KERNEL_FUSED
+    if torch.cuda.get_device_properties(0).multi_processor_count != 152:
+        pytest.skip("heights stated for 152 SMs")
+    expect = {(200, 50): 1, (1024, 128): 4, (4096, 512): 31, (100, 300): 2}
+    for (nx, ny), rows in expect.items():
+        lat = Lattice(nx, ny, inputs.base_params(), kernel=KERNEL_FUSED)
+        info = lat.info()
+        lat.close()
+        assert (info["tile_cols"], info["tile_rows"]) == (118, rows), (nx, ny, info)
+
+
+@pytest.mark.parametrize("tile", ["118,1", "118,3", "60,7", "37,50", "118,16"])
+def test_results_do_not_depend_on_the_tiling(tile, monkeypatch):
+    """Every node is computed by the same instructions whichever CTA owns it (halo
+    nodes are recomputed, not exchanged), so any tiling gives the same bits."""
+    from paper_1803_01756_gb300.lattice import Lattice, KERNEL_FUSED
+    w = inputs.workload("channel_200x50")
+    rho0 = inputs.initial_density(w)
+
+    def run():
+        lat = Lattice(w["nx"], w["ny"], w["params"], kernel=KERNEL_FUSED)
+        lat.write_fields(rho0)
+        lat.step(200)
+        out, info = lat.read_fields(), lat.info()
+        lat.close()
+        return out, (info["tile_cols"], info["tile_rows"])
+
+    ref, t_ref = run()
+    monkeypatch.setenv("LBM_FUSED_TILE", tile)
+    got, t_got = run()
+    assert t_got == tuple(int(v) for v in tile.split(","))
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b), (t_ref, t_got)
+
+
+@pytest.mark.parametrize("over", [dict(), dict(thermal=0), dict(x_bc=2, p_amp_frac=0.1,
+                                                                u_period=60.0)])
+def test_graph_replay_equals_one_launch_per_update(over):
+    """lbm_step's graph chunks (16 updates, captured per buffer parity) give the same
+    bits as one launch per update, across call lengths that start chunks at both
+    parities and with per-launch timing switched on in between."""
+    from paper_1803_01756_gb300.lattice import Lattice, KERNEL_FUSED
+    nx, ny = 150, 40
+    p = inputs.base_params(**{"u_amp": 0.03, "u_period": 50.0, **over})
+    rho0 = inputs.noisy_density(nx, ny, inputs.RHO_V_086, 0.01, seed=21)
+    out = []
+    for graph in (True, False):
+        lat = Lattice(nx, ny, p, kernel=KERNEL_FUSED)
+        lat.set_graph(graph)
+        lat.write_fields(rho0)
+        lat.step(5)
+        lat.step(40)
+        lat.timing_enable(True)
+        lat.step(17)
+        lat.timing_enable(False)
+        lat.step(37)
+        lat.step(32)
+        assert lat.t == 131
+        out.append(lat.read_fields())
+        lat.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
