@@ -525,7 +525,7 @@ def main():
                     help="lattice: MLUPS of one channel; batch: one launch per update over 96 "
                          "channels; serve: the job server")
     ap.add_argument("--jobs", type=int, default=160)
-    ap.add_argument("--job-steps", type=int, default=2000)
+    ap.add_argument("--job-steps", type=int, default=10000)
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--chunk-steps", type=int, default=250)
     ap.add_argument("--traffic", type=float, default=None,
