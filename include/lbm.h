@@ -122,7 +122,9 @@ int lbm_write_fields(lbm_h h, const double *rho, const double *T, void *stream);
    fused path the updates go in chunks of 16, each preceded by a 192-byte copy of its
    boundary scalars from pinned host memory, and the host may wait for the copy of the
    chunk before last.  Calls on different streams must be ordered by the caller (they
-   share the lattice state). */
+   share the lattice state).  LBM_ERR_ARG if the stream is being captured into a CUDA
+   graph: each call stages the boundary scalars of its own updates, so a captured call
+   could not be replayed (lbm_set_graph replays whole chunks instead). */
 int lbm_step(lbm_h h, long nsteps, void *stream);
 
 /* enable != 0 (the default): lbm_step replays each full chunk of 16 fused updates from a
@@ -180,13 +182,16 @@ typedef struct lbm_batch *lbm_batch_h;
 /* LBM_ERR_ARG if a lattice is NULL, repeated, on another device, not on the fused
    kernel, or differs in modes or storage from the first. */
 int lbm_batch_create(lbm_h *lattices, int n, lbm_batch_h *out);
-/* Advance every lattice of the batch by nsteps updates (enqueued on the stream). */
+/* Advance every lattice of the batch by nsteps updates (enqueued on the stream).
+   LBM_ERR_ARG if the stream is being captured into a CUDA graph, as for lbm_step. */
 int lbm_batch_step(lbm_batch_h b, long nsteps, void *stream);
 /* enable != 0: replay whole chunks of 16 steps from one captured CUDA graph. */
 int lbm_batch_set_graph(lbm_batch_h b, int enable);
 /* Output rows per tile (the work-list granularity).  The default, chosen at creation, is the
-   height among 128, 96, 64, 48, 32, 24, 16 rows whose work-list a greedy schedule over the
-   resident CTAs finishes first. */
+   height among 128, 96, 64, 48, 32, 24 and 16 rows whose work-list a greedy schedule over
+   the resident CTAs finishes first; if that leaves fewer tiles than SMs, heights down to
+   1 row compete, with row steps slower the more tiles share an SM.  A launch has one CTA
+   per tile when there are fewer tiles than resident CTAs. */
 int lbm_batch_set_tile_rows(lbm_batch_h b, int rows);
 /* Time tile heights 16..128 rows with steps_per_candidate timed updates each (plus two
    warm-up updates) and keep the fastest.  These are real updates: every lattice

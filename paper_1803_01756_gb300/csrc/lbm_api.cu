@@ -589,6 +589,11 @@ int lbm_step(lbm_h h, long nsteps, void *stream) {
   if (!h || nsteps < 0) return LBM_ERR_ARG;
   LBM_CUDA(cudaSetDevice(h->device));
   cudaStream_t s = (cudaStream_t)stream;
+  // each call stages the boundary scalars of its own updates, so a captured call could
+  // not be replayed; whole chunks are replayed from the handle's own graphs instead
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  LBM_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return LBM_ERR_ARG;
   if (h->kernel == LBM_KERNEL_FUSED) return fused_steps(h, nsteps, s);
   for (long k = 0; k < nsteps; k++) {
     int rc = split_update(h, s);

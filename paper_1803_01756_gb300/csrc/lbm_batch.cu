@@ -16,7 +16,7 @@ struct lbm_batch {
   lbm::DevParams mode{};  // boundary modes and physics switches shared by all lattices
   std::vector<lbm_lattice *> lat;  // work-list order: most tiles first
   int tile_rows = 64;              // output rows per tile (default_rows, or set / autotuned)
-  int ntiles = 0, grid = 0;
+  int ntiles = 0, grid = 0, sms = 1;
   BatchChannel *d_ch[2] = {nullptr, nullptr};  // tables for even and odd steps of a call
   std::vector<BatchChannel> h_ch[2];
   StepScalars *d_sc = nullptr;                  // [chunk][n] scalars of the next chunk
@@ -59,40 +59,73 @@ void layout(lbm_batch *b) {
   drop_graph(b);
 }
 
-// Default tile height.  Each candidate height is scored by the makespan of a greedy
-// list schedule of the work-list (tiles in launch order, each taken by the first free
-// CTA slot of `grid`, a tile costing its row steps H + 15) and the shortest wins, the
-// taller on a tie.  Measured on GB300 against fixed heights, this picks the best or
-// within 4 % of it on four shapes: 12 channels of 512 x 64 (16 rows, 2.8x the 64-row
-// rate), 20 of 1024 x 256, one of 4096 x 512 and 96 uneven channels.
+// Greedy list schedule of the work-list at tile height H over `grid` CTA slots (tiles in
+// launch order, each taken by the first free slot, a tile costing its row steps H + 15):
+// returns the makespan in row steps and the number of tiles.
+double schedule(const lbm_batch *b, const std::vector<const lbm_lattice *> &order, int H,
+                long long &ntiles) {
+  const int W = lbm::fused_max_width();
+  std::priority_queue<double, std::vector<double>, std::greater<double>> slots;
+  for (int k = 0; k < b->grid; k++) slots.push(0.0);
+  double makespan = 0.0;
+  ntiles = 0;
+  for (const lbm_lattice *h : order) {
+    const int rows = std::min(H, h->ny), strips = (h->nx + W - 1) / W;
+    for (int y0 = 0; y0 < h->ny; y0 += rows) {
+      const double len = std::min(rows, h->ny - y0) + 15.0;
+      for (int x = 0; x < strips; x++) {
+        const double t = slots.top() + len;
+        slots.pop();
+        slots.push(t);
+        makespan = std::max(makespan, t);
+        ntiles++;
+      }
+    }
+  }
+  return makespan;
+}
+
+// Default tile height.  Each candidate of 128 .. 16 rows is scored by the makespan of its
+// greedy schedule and the shortest wins, the taller on a tie.  Measured on GB300 against
+// fixed heights, this picks the best or within 4 % of it on four shapes: 12 channels of
+// 512 x 64 (16 rows, 2.8x the 64-row rate), 20 of 1024 x 256, one of 4096 x 512 and 96
+// uneven channels.  When that leaves fewer tiles than SMs, most of the GPU would idle:
+// then heights down to one row compete, each makespan weighted by the time of a row step
+// with k tiles per SM (relative 0.85, 0.97, 1.42, 1.64 for k = 1 .. 4: one CTA alone is
+// bound by the latency of its row step, four share the issue slots), so that a few small
+// lattices spread over the SMs (200 x 50 alone: 1 row, 17.0 against 39.3 us per update
+// with 16; 1024 x 128: 4 rows, 22.8 against 39.6 us).
 int default_rows(const lbm_batch *b) {
-  static const int candidates[] = {128, 96, 64, 48, 32, 24, 16};
+  static const int tall[] = {128, 96, 64, 48, 32, 24, 16};
+  static const int small[] = {16, 12, 8, 6, 4, 3, 2, 1};
+  static const double kStep[5] = {0.0, 0.85, 0.97, 1.42, 1.64};
   std::vector<const lbm_lattice *> order(b->lat.begin(), b->lat.end());
   std::stable_sort(order.begin(), order.end(), [](const lbm_lattice *x, const lbm_lattice *y) {
     return (long long)x->nx * x->ny > (long long)y->nx * y->ny;
   });
-  const int W = lbm::fused_max_width();
   int best = 16;
+  long long best_tiles = 0;
   double best_cost = 0.0;
-  for (int H : candidates) {
-    std::priority_queue<double, std::vector<double>, std::greater<double>> slots;
-    for (int k = 0; k < b->grid; k++) slots.push(0.0);
-    double makespan = 0.0;
-    for (const lbm_lattice *h : order) {
-      const int rows = std::min(H, h->ny), strips = (h->nx + W - 1) / W;
-      for (int y0 = 0; y0 < h->ny; y0 += rows) {
-        const double len = std::min(rows, h->ny - y0) + 15.0;
-        for (int x = 0; x < strips; x++) {
-          const double t = slots.top() + len;
-          slots.pop();
-          slots.push(t);
-          makespan = std::max(makespan, t);
-        }
-      }
-    }
-    if (best_cost == 0.0 || makespan < best_cost) {
+  for (int H : tall) {
+    long long n = 0;
+    const double cost = schedule(b, order, H, n);
+    if (best_cost == 0.0 || cost < best_cost) {
       best = H;
-      best_cost = makespan;
+      best_cost = cost;
+      best_tiles = n;
+    }
+  }
+  if (best_tiles >= b->sms) return best;
+  const int occ = std::max(1, std::min(4, b->grid / b->sms));
+  best_cost = 0.0;
+  for (int H : small) {
+    long long n = 0;
+    const double span = schedule(b, order, H, n);
+    const int k = (int)std::max(1LL, std::min<long long>(occ, (n + b->sms - 1) / b->sms));
+    const double cost = span * kStep[k];
+    if (best_cost == 0.0 || cost < best_cost) {
+      best = H;
+      best_cost = cost;
     }
   }
   return best;
@@ -130,11 +163,14 @@ int upload_tables(lbm_batch *b, cudaStream_t s) {
   return LBM_OK;
 }
 
+// CTAs of one launch: the resident grid, or one per tile when there are fewer tiles
+int launch_grid(const lbm_batch *b) { return std::min(b->grid, b->ntiles); }
+
 int launch_one(lbm_batch *b, int k, cudaStream_t s) {
   const int n = (int)b->lat.size();
   return cuda_fail(lbm::launch_fused_batch(b->mode, b->storage, b->d_ch[k & 1], n,
                                            b->d_sc + (size_t)k * n, b->ntiles, b->d_counter,
-                                           b->grid, s));
+                                           launch_grid(b), s));
 }
 
 int build_graph(lbm_batch *b) {
@@ -189,6 +225,9 @@ int lbm_batch_create(lbm_h *lattices, int n, lbm_batch_h *out) {
   b->lat.assign(lattices, lattices + n);
   cudaError_t e = cudaSetDevice(b->device);
   b->grid = e == cudaSuccess ? lbm::fused_batch_grid(b->mode, b->storage, b->device) : 0;
+  if (b->grid > 0 &&
+      cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+    b->grid = 0;
   if (b->grid < 1) {
     delete b;
     return LBM_ERR_CUDA;
@@ -217,6 +256,9 @@ int lbm_batch_step(lbm_batch_h b, long nsteps, void *stream) {
   if (!b || nsteps < 0) return LBM_ERR_ARG;
   LBM_CUDA(cudaSetDevice(b->device));
   cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  LBM_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return LBM_ERR_ARG;  // as lbm_step
   int rc = upload_tables(b, s);
   if (rc) return rc;
   const int n = (int)b->lat.size();
@@ -246,7 +288,7 @@ int lbm_batch_step(lbm_batch_h b, long nsteps, void *stream) {
         const int par = (phase + k) & 1;
         rc = cuda_fail(lbm::launch_fused_batch(b->mode, b->storage, b->d_ch[par], n,
                                                b->d_sc + (size_t)k * n, b->ntiles, b->d_counter,
-                                               b->grid, s));
+                                               launch_grid(b), s));
         if (rc) return rc;
       }
     }

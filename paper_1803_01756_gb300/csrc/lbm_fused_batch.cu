@@ -7,8 +7,10 @@ namespace lbm {
 namespace {
 
 // Persistent batched update: resident CTAs take tiles of many lattices from one
-// work-list through an atomic counter (largest lattices first), so uneven lattice
-// sizes balance across the SMs.  The last CTA to leave resets the counters.
+// work-list (largest lattices first), so uneven lattice sizes balance across the SMs.
+// Block b starts with tile b (consecutive blocks sit on different SMs, so a batch with
+// fewer tiles than SMs runs one tile per SM); later tiles come from an atomic counter.
+// The last CTA to leave resets the counters.
 // (Reading the bulk physics from a constant-bank copy when all lattices share it
 // measured 2 % faster than the shared-memory copy used here, and a kernel holding
 // both paths 12 % slower, so there is one path.)
@@ -20,9 +22,9 @@ __global__ void __launch_bounds__(FNT, LBM_FUSED_MIN_CTAS)
   FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
   __shared__ DevParams sp;
   __shared__ int s_tile, s_ch;
+  int tile = (int)blockIdx.x;  // thread 0: the CTA's next tile
   for (;;) {
     if (threadIdx.x == 0) {
-      const int tile = atomicAdd(&counter[0], 1);
       int k = 0;
       if (tile < ntiles) {
         int lo = 0, hi = nch - 1;  // last channel whose first tile <= tile
@@ -37,8 +39,8 @@ __global__ void __launch_bounds__(FNT, LBM_FUSED_MIN_CTAS)
       s_ch = k;
     }
     __syncthreads();
-    const int tile = s_tile;
-    if (tile >= ntiles) break;
+    const int cur = s_tile;
+    if (cur >= ntiles) break;
     const BatchChannel &C = ch[s_ch];
     {
       // the lattice parameters live in shared memory for the tile
@@ -47,7 +49,7 @@ __global__ void __launch_bounds__(FNT, LBM_FUSED_MIN_CTAS)
       for (int i = threadIdx.x; i < (int)(sizeof(DevParams) / sizeof(int)); i += FNT) dst[i] = src[i];
     }
     __syncthreads();
-    const int local = tile - C.tile_begin;
+    const int local = cur - C.tile_begin;
     const int bx = local % C.strips, by = local / C.strips;
     const int Y0 = by * C.H;
     const typename ST::T *gs = static_cast<const typename ST::T *>(C.gs);
@@ -55,6 +57,7 @@ __global__ void __launch_bounds__(FNT, LBM_FUSED_MIN_CTAS)
     fused_tile<YW, XO, TH, MP, ST, 1>(sp, sp, gs, gout, C.Tin, C.Tout, C.status, sc[s_ch], bx * C.W,
                                    C.W, Y0, min(Y0 + C.H, sp.ny), S);
     __syncthreads();
+    if (threadIdx.x == 0) tile = (int)gridDim.x + atomicAdd(&counter[0], 1);
   }
   if (threadIdx.x == 0 && atomicAdd(&counter[1], 1) == (int)gridDim.x - 1) {
     counter[0] = 0;

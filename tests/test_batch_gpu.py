@@ -119,7 +119,15 @@ def test_default_tile_height_follows_the_batch_size():
     info = b.info()
     assert info["tile_rows"] >= 24 and info["tiles"] <= info["grid"]
     b.close()
-    for lat in small + [big]:
+    # fewer tiles than SMs at 16 rows: heights below 16 spread the lattice over the SMs
+    tiny = Lattice(200, 50, inputs.base_params(), kernel=2)
+    b = Batch([tiny])
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    info = b.info()
+    assert info["tile_rows"] < 16 and 16 <= info["tiles"] <= sms, info
+    b.close()
+    for lat in small + [big, tiny]:
         lat.close()
 
 

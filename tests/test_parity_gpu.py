@@ -379,3 +379,25 @@ def test_graph_replay_equals_one_launch_per_update(over):
         lat.close()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+def test_step_refuses_a_stream_under_capture():
+    """A caller's CUDA-graph capture of lbm_step is refused before anything is enqueued
+    (the boundary scalars of each call are staged for its own updates); the handle keeps
+    working afterwards."""
+    import torch
+    from paper_1803_01756_gb300.lattice import Lattice, LbmError, KERNEL_FUSED
+    lat = Lattice(64, 24, inputs.base_params(), kernel=KERNEL_FUSED)
+    lat.write_fields(inputs.noisy_density(64, 24, inputs.RHO_V_086, 0.01, seed=4))
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with pytest.raises(LbmError) as ei:
+        with torch.cuda.graph(g, stream=s):
+            lat.step(16)
+    assert ei.value.code == -1
+    torch.cuda.synchronize()
+    lat.step(16)
+    assert lat.t == 16
+    rho = lat.read_fields()[0]
+    assert np.isfinite(rho).all()
+    lat.close()
