@@ -115,14 +115,20 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
     const double rphi = 1.0 + kap * (1.0 - sr);
     const double P = rr * p.eos_R * Tr / (1.0 - b * rr) - p.eos_a * rphi * rphi * rr * rr / Dr;
     const double psi2 = p.G != 0.0 ? 2.0 * (P - rr / 3.0) / p.G : 0.0;
-    d.inv_1mbr = (float)(1.0 / (1.0 - b * rr));
-    d.inv_Dr = (float)(1.0 / Dr);
+    const double tG = p.G != 0.0 ? 2.0 / p.G : 0.0;
     d.sr = (float)sr;
     d.rphi_r = (float)rphi;
-    d.phi_r = (float)(rphi * rphi);
+    d.kappa1 = (float)(1.0 + kap);
     d.psi_r2 = (float)(psi2 > 0.0 ? psi2 : 0.0);
     d.psi_r = (float)std::sqrt(psi2 > 0.0 ? psi2 : 0.0);
-    d.two_over_G = p.G != 0.0 ? (float)(2.0 / p.G) : 0.0f;
+    d.ps_RT = (float)(tG * p.eos_R);
+    d.ps_R = (float)(tG * p.eos_R * Tr / (1.0 - b * rr));
+    d.ps_g = (float)(1.0 + 2.0 * b * rr);
+    d.ps_B = (float)(tG * p.eos_a * rphi * rphi / Dr);
+    d.ps_phi = (float)(-tG * p.eos_a * kap);
+    d.ps_3 = (float)(-tG / 3.0);
+    d.G3 = (float)(-p.G / 3.0);
+    d.G3r = (float)(-p.G / 3.0 * std::sqrt(psi2 > 0.0 ? psi2 : 0.0));
     d.wall_r = (float)((p.G - p.Gw) * std::sqrt(psi2 > 0.0 ? psi2 : 0.0));
     d.drho_ref_g = (float)(rr - p.rho_g);
   }
@@ -132,9 +138,9 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
     const double se = p.s_e, sz = p.s_zeta, sq = p.s_q;
     const double cte = 12.0 * p.theta * se * p.G * p.G, ctz = 12.0 * p.theta * sz * p.G * p.G;
     const double k1[5] = {(1.0 - se) / 36.0, -2.0 * se / 36.0, se / 36.0,
-                          (1.0 - 0.5 * se) * 6.0 / 36.0, cte / 36.0};
+                          (1.0 - 0.5 * se) * 6.0 / 36.0, cte / 36.0 / 9.0};
     const double k2[5] = {(1.0 - sz) / 36.0, sz / 36.0, -sz / 36.0,
-                          -(1.0 - 0.5 * sz) * 6.0 / 36.0, -ctz / 36.0};
+                          -(1.0 - 0.5 * sz) * 6.0 / 36.0, -ctz / 36.0 / 9.0};
     const double kq[3] = {(1.0 - sq) / 12.0, -sq / 12.0, -(1.0 - 0.5 * sq) / 12.0};
     for (int i = 0; i < 5; i++) {
       d.k1[i] = (float)k1[i];
@@ -151,6 +157,13 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
   d.inv_drho = p.rho_l != p.rho_g ? (float)(1.0 / (p.rho_l - p.rho_g)) : 0.0f;
   d.tau_const = p.tau_g == p.tau_l || p.rho_l == p.rho_g;
   d.s_nu_const = (float)(1.0 / p.tau_g);
+  {
+    const double sn = 1.0 / p.tau_g;
+    d.kn[0] = (float)(0.25 * (1.0 - sn));
+    d.kn[1] = (float)(0.25 * sn);
+    d.kn[2] = (float)(0.25 * (2.0 - sn));
+    d.kn[3] = (float)(0.25 * (1.0 - 0.5 * sn));
+  }
   d.gx = (float)p.gx;
   d.gy = (float)p.gy;
   d.has_g = p.gx != 0.0 || p.gy != 0.0;

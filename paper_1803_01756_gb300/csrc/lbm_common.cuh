@@ -74,27 +74,35 @@ struct DevParams {
   float Tc, inv_Tc;
   float eos_a, eos_b, eos_R, kappa;
   float G, Gw, rho_w;     // rho_w <= 0: psi_w = local psi
-  // reference state (rho_ref, T_ref) of the deviation pseudopotential
-  float inv_1mbr;         // 1 / (1 - b rho_ref)
-  float inv_Dr;           // 1 / (1 + 2 b rho_ref - b^2 rho_ref^2)
+  // reference state (rho_ref, T_ref) of the deviation pseudopotential, with D(rho) =
+  // 1 + 2 b rho - b^2 rho^2 and the factor 2/G of psi^2 folded into the coefficients
   float sr;               // sqrt(T_ref / Tc)
   float rphi_r;           // 1 + kappa (1 - sr)
-  float phi_r;            // rphi_r^2
+  float kappa1;           // 1 + kappa
   float psi_r, psi_r2;    // psi(rho_ref, T_ref) and its square
-  float two_over_G;
+  float ps_RT;            // (2/G) R
+  float ps_R;             // (2/G) R T_ref / (1 - b rho_ref)
+  float ps_g;             // 1 + 2 b rho_ref
+  float ps_B;             // (2/G) a phi(T_ref) / D(rho_ref)
+  float ps_phi;           // -(2/G) a kappa
+  float ps_3;             // -(2/G) / 3
+  float G3, G3r;          // -G / 3 and -G psi_r / 3 (bulk Eq. 9 force, 1/3 weight taken out)
   float wall_r;           // (G - Gw) psi_r: wall term of Eqs. 9 + 14 at the reference state
   float drho_ref_g;       // rho_ref - rho_g, the reference part of Eq. 15's (rho - rho_v)
   float c_theta_e;        // 12 theta s_e G^2   ((1 - s_e/2) 12 theta / (tau_e - 1/2) = 12 theta s_e)
   float c_theta_z;        // 12 theta s_zeta G^2
   float s_e, s_z, s_q;
   // collision coefficients with the 1/D_k of M^-1 = M^T D^-1 folded in (Eqs. 7-8):
-  //   a1 = m1*/36 = k1[0] n1 + k1[1] drho + k1[2] 3rho|u|^2 + k1[3] u.F + k1[4] |q|^2
-  //   a2 = m2*/36 = k2[0] n2 + k2[1] drho + k2[2] 3rho|u|^2 + k2[3] u.F + k2[4] |q|^2
+  //   a1 = m1*/36 = k1[0] n1 + k1[1] drho + k1[2] 3rho|u|^2 + k1[3] u.F + k1[4] 9|q|^2
+  //   a2 = m2*/36 = k2[0] n2 + k2[1] drho + k2[2] 3rho|u|^2 + k2[3] u.F + k2[4] 9|q|^2
   //   a4 = m4*/12 = kq[0] n4 + kq[1] rho u_x + kq[2] F_x   (same for a6 with y)
   float k1[5], k2[5], kq[3];
   float tau_g, dtau, rho_g, inv_drho;  // Eq. 5: tau_g + clamp((rho - rho_g) inv_drho) dtau
   int tau_const;          // tau_g == tau_l
   float s_nu_const;
+  // with tau_const, the a7 / a8 coefficients of the collision (see collide):
+  // 0.25 (1 - s_nu), 0.25 s_nu, 0.25 (2 - s_nu), 0.25 (1 - s_nu / 2)
+  float kn[4];
   float gx, gy;
   int has_g;              // gx or gy nonzero
   float Cv, lambda;
@@ -163,29 +171,27 @@ __device__ __forceinline__ float pseudopotential(const DevParams &p, float rho, 
 // Deviation of psi from psi_r = psi(rho_ref, T_ref), from the deviations
 // drho = rho - rho_ref and dT = T - T_ref.  The pressure difference of Eq. 11 is
 // formed term by term from exact difference identities,
-//   rho/(1-b rho) - rho_r/(1-b rho_r) = drho / ((1-b rho)(1-b rho_r)),
-//   rho^2/D(rho) - rho_r^2/D(rho_r)   = drho (rho + rho_r + 2 b rho rho_r) / (D(rho) D(rho_r)),
-//   phi(T) - phi(T_r) = -kappa (s - s_r) (r + r_r),  s - s_r = dT / (Tc (s + s_r)),
+//   rho T/(1-b rho) - rho_r T_r/(1-b rho_r) = (dT rho + T_r drho/(1-b rho_r)) / (1-b rho),
+//   phi rho^2/D(rho) - phi_r rho_r^2/D(rho_r)
+//       = (dphi rho^2 + phi_r drho (rho + rho_r + 2 b rho rho_r) / D(rho_r)) / D(rho),
+//   dphi = phi(T) - phi(T_r) = -kappa (s - s_r) (r + r_r),  s - s_r = dT / (Tc (s + s_r)),
 // so no large nearly equal numbers are subtracted; then
 //   psi^2 - psi_r^2 = 2 (dP - drho/3) / G   and   psi - psi_r = (psi^2 - psi_r^2) / (psi + psi_r).
 // Neighbour differences of psi therefore keep FP32 relative precision.
 __device__ __forceinline__ float pseudopotential_dev(const DevParams &p, float drho, float dT,
                                                      unsigned &st) {
   const float rho = p.rho_ref + drho;
-  const float T = p.T_ref + dT;
   const float br = p.eos_b * rho;
   const float inv1 = __fdividef(1.0f, 1.0f - br);
-  const float invD = __fdividef(1.0f, 1.0f + 2.0f * br - br * br);
-  const float A = rho * inv1;
-  const float B = rho * rho * invD;
-  const float dA = drho * inv1 * p.inv_1mbr;
-  const float dB = drho * (rho + p.rho_ref + 2.0f * br * p.rho_ref) * invD * p.inv_Dr;
-  const float s = sqrtf(T * p.inv_Tc);
+  const float invD = __fdividef(1.0f, fmaf(br, 2.0f - br, 1.0f));
+  const float s = sqrtf((p.T_ref + dT) * p.inv_Tc);
   const float ds = __fdividef(dT * p.inv_Tc, s + p.sr);
-  const float r = 1.0f + p.kappa * (1.0f - s);
-  const float dphi = -p.kappa * ds * (r + p.rphi_r);
-  const float dP = p.eos_R * (dT * A + p.T_ref * dA) - p.eos_a * (dphi * B + p.phi_r * dB);
-  const float dpsi2 = p.two_over_G * (dP - drho * (1.0f / 3.0f));
+  const float r = fmaf(-p.kappa, s, p.kappa1);
+  const float g = fmaf(rho, p.ps_g, p.rho_ref);
+  // (2/G) R of the pressure difference, and (2/G) a of its attraction part
+  const float tR = inv1 * fmaf(p.ps_RT * dT, rho, p.ps_R * drho);
+  const float tA = invD * fmaf(p.ps_phi * ds * (r + p.rphi_r), rho * rho, p.ps_B * drho * g);
+  const float dpsi2 = fmaf(p.ps_3, drho, tR - tA);
   const float psi2 = p.psi_r2 + dpsi2;
   if (!(psi2 >= 0.0f)) {
     st |= ST_PSI_NEG;
@@ -305,7 +311,7 @@ __device__ __forceinline__ float sum9(const float g[9]) {
 // as psi_w is
 //   F = psi_c [ -G sum_fluid w dpsi e + ((G - Gw) psi_r - Gw dpsi_c) s ],
 // written so that no two psi-sized terms cancel in FP32.
-// Returns F and |F_m|^2 / psi^2 = G^2 |q|^2 (G^2 folded into c_theta).
+// Returns F and 9 |F_m|^2 / psi^2 = 9 G^2 |q|^2 (9 G^2 folded into c_theta).
 // ---------------------------------------------------------------------------
 struct Force {
   float Fx, Fy, fm2;
@@ -333,14 +339,14 @@ __device__ __forceinline__ Force interaction_force(const DevParams &p, float dps
   F.Fx = psi_c * (-p.G * qx + wc * sx);
   F.Fy = psi_c * (-p.G * qy + wc * sy);
   const float fx = qx - p.psi_r * sx, fy = qy - p.psi_r * sy;
-  F.fm2 = fx * fx + fy * fy;
+  F.fm2 = 9.0f * (fx * fx + fy * fy);
   return F;
 }
 
 // ---------------------------------------------------------------------------
 // Moment-space collision of Eq. 7 with Li's forcing (Eq. 8), written in closed
 // form on the deviation populations.  In: pulled g, their sum drho = sum9(g),
-// total force F, fm2 = |sum w psi e|^2.  Out: post-collision deviations gs.
+// total force F, fm2 = 9 |sum w psi e|^2.  Out: post-collision deviations gs.
 // Returns rho and u.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void collide(const DevParams &p, const float g[9], float drho, float Fx,
@@ -367,12 +373,21 @@ __device__ __forceinline__ void collide(const DevParams &p, const float g[9], fl
   const float uu3 = 3.0f * (jxe * ux + jye * uy);  // 3 rho |u|^2
   const float uF = ux * Fx + uy * Fy;
 
-  float s_nu;
+  // coefficients of a7 and a8 below: 0.25 (1 - s_nu), 0.25 s_nu, 0.25 (2 - s_nu) and
+  // 0.25 (1 - s_nu / 2), from the parameters when s_nu is constant
+  float c7a, c7b, c7c, c8c;
   if (p.tau_const) {
-    s_nu = p.s_nu_const;
+    c7a = p.kn[0];
+    c7b = p.kn[1];
+    c7c = p.kn[2];
+    c8c = p.kn[3];
   } else {
     float fr = fminf(fmaxf((rho - p.rho_g) * p.inv_drho, 0.0f), 1.0f);
-    s_nu = __fdividef(1.0f, p.tau_g + fr * p.dtau);  // Eq. 5
+    const float s_nu = __fdividef(1.0f, p.tau_g + fr * p.dtau);  // Eq. 5
+    c7b = 0.25f * s_nu;
+    c7a = 0.25f - c7b;
+    c7c = 0.5f - c7b;
+    c8c = fmaf(-0.5f, c7b, 0.25f);
   }
 
   // m* - rho_ref c, moment by moment (Eq. 7) with (1 - s/2) S from Eq. 8, each already
@@ -384,24 +399,23 @@ __device__ __forceinline__ void collide(const DevParams &p, const float g[9], fl
   const float a4 = p.kq[0] * n4 + p.kq[1] * jxe + p.kq[2] * Fx;
   const float a5 = (jy + Fy) * (1.0f / 6.0f);
   const float a6 = p.kq[0] * n6 + p.kq[1] * jye + p.kq[2] * Fy;
-  const float a7 = 0.25f * ((1.0f - s_nu) * n7 + s_nu * (jxe * ux - jye * uy) +
-                            (2.0f - s_nu) * (ux * Fx - uy * Fy));
-  const float a8 = 0.25f * ((1.0f - s_nu) * n8 + s_nu * (jxe * uy) +
-                            (1.0f - 0.5f * s_nu) * (ux * Fy + uy * Fx));
+  const float a7 = c7a * n7 + c7b * (jxe * ux - jye * uy) + c7c * (ux * Fx - uy * Fy);
+  const float a8 = c7a * n8 + c7b * (jxe * uy) + c8c * (ux * Fy + uy * Fx);
   // f* = M^-1 m* = M^T D^-1 m*
   const float b_ax = a0 - a1 - 2.0f * a2;   // common part of f1..f4
   const float b_dg = a0 + 2.0f * a1 + a2;   // common part of f5..f8
   const float px = a3 - 2.0f * a4, py = a5 - 2.0f * a6;
-  const float qx = a3 + a4, qy = a5 + a6;
+  const float qs = (a3 + a4) + (a5 + a6), qd = (a5 + a6) - (a3 + a4);
+  const float bxp = b_ax + a7, bxm = b_ax - a7, bdp = b_dg + a8, bdm = b_dg - a8;
   gs[0] = a0 - 4.0f * a1 + 4.0f * a2;
-  gs[1] = b_ax + px + a7;
-  gs[2] = b_ax + py - a7;
-  gs[3] = b_ax - px + a7;
-  gs[4] = b_ax - py - a7;
-  gs[5] = b_dg + qx + qy + a8;
-  gs[6] = b_dg - qx + qy - a8;
-  gs[7] = b_dg - qx - qy + a8;
-  gs[8] = b_dg + qx - qy - a8;
+  gs[1] = bxp + px;
+  gs[2] = bxm + py;
+  gs[3] = bxp - px;
+  gs[4] = bxm - py;
+  gs[5] = bdp + qs;
+  gs[6] = bdm + qd;
+  gs[7] = bdp - qs;
+  gs[8] = bdm - qd;
   rho_out = rho;
   ux_out = ux;
   uy_out = uy;

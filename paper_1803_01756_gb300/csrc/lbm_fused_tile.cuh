@@ -65,7 +65,7 @@ __device__ __forceinline__ int modi(int v, int n) {
 // K(T) of Eq. 16 at one node from a 3-row ring window of the stage field, with
 //   grad T = 3 sum w_i T(x+e_i) e_i = g / 3,    g_x = (T1 - T3) + (T5 - T7 + T8 - T6) / 4,
 //   lap T = 6 sum w_i (T(x+e_i) - T(x)) = 2 L / 3,
-//                                         L = (T1 + T2 + T3 + T4 - 4T) + (T5 + T6 + T7 + T8 - 4T) / 4,
+//                                         L = (T1 + T2 + T3 + T4) + (T5 + T6 + T7 + T8) / 4 - 5T,
 //   T (dP/dT)_rho div u / (rho Cv) = e1 T + e2 s (1 + kappa - kappa s),  s = sqrt(T/Tc),
 // and, with x = T/Tc = s^2, the last term equal to E1 x + E2 s (E1 = e1 Tc - e2 kappa,
 // E2 = e2 (1 + kappa)).  The caller passes us = u/3, cl = (2/3) lambda/(rho Cv), E1, E2:
@@ -76,10 +76,10 @@ __device__ __forceinline__ float rk_rate(const DevParams &p, float *__restrict__
   const float c = F1(R, i0);
   const float v1 = F1(R, i0 + 4), v3 = F1(R, i0 - 4), v2 = F1(R, ip), v4 = F1(R, im);
   const float v5 = F1(R, ip + 4), v6 = F1(R, ip - 4), v7 = F1(R, im - 4), v8 = F1(R, im + 4);
-  const float d57 = v5 - v7;
-  const float gx = (v1 - v3) + 0.25f * (d57 + (v8 - v6));
-  const float gy = (v2 - v4) + 0.25f * (d57 + (v6 - v8));
-  const float lap = ((v1 + v3) + (v2 + v4) - 4.0f * c) + 0.25f * ((v5 + v7) + (v6 + v8) - 4.0f * c);
+  const float d57 = v5 - v7, d86 = v8 - v6;
+  const float gx = fmaf(0.25f, d57 + d86, v1 - v3);
+  const float gy = fmaf(0.25f, d57 - d86, v2 - v4);
+  const float lap = fmaf(-5.0f, c, fmaf(0.25f, (v5 + v7) + (v6 + v8), (v1 + v3) + (v2 + v4)));
   const float x = fmaf(c, p.inv_Tc, p.xr);  // T/Tc > 0 on fluid nodes
   const float s = x * rsqrtf(x);
   return -(uxs * gx + uys * gy) + cl * lap - E1 * x - E2 * s;
@@ -261,15 +261,15 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
             dn[8] = F1(ring_psi, pm + 4);
             const float dpc = F1(ring_psi, p0);
             if (!sdn && !sup) {
-              // no wall neighbour: F = -G psi sum w dpsi e  (Eq. 9; sum w e = 0)
-              const float qx = (1.0f / 3.0f) * (dn[1] - dn[3]) +
-                               (1.0f / 12.0f) * ((dn[5] - dn[7]) + (dn[8] - dn[6]));
-              const float qy2 = (1.0f / 3.0f) * (dn[2] - dn[4]) +
-                                (1.0f / 12.0f) * ((dn[5] - dn[7]) + (dn[6] - dn[8]));
-              const float gpsi = -p.G * (p.psi_r + dpc);
-              F.Fx = gpsi * qx;
-              F.Fy = gpsi * qy2;
-              F.fm2 = qx * qx + qy2 * qy2;
+              // no wall neighbour: F = -G psi sum w dpsi e  (Eq. 9; sum w e = 0), with
+              // Q = 3 sum w dpsi e and fm2 = |Q|^2 = 9 |q|^2
+              const float d57 = dn[5] - dn[7], d86 = dn[8] - dn[6];
+              const float Qx = fmaf(0.25f, d57 + d86, dn[1] - dn[3]);
+              const float Qy = fmaf(0.25f, d57 - d86, dn[2] - dn[4]);
+              const float gpsi = fmaf(p.G3, dpc, p.G3r);  // -G psi / 3
+              F.Fx = gpsi * Qx;
+              F.Fy = gpsi * Qy;
+              F.fm2 = fmaf(Qx, Qx, Qy * Qy);
             } else {
               unsigned solid_mask = 0u;
               if (sup) solid_mask |= (1u << 2) | (1u << 5) | (1u << 6);
