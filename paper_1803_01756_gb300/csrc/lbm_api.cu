@@ -137,9 +137,9 @@ DevParams derive(int nx, int ny, int pitch, const lbm_params_t &p, double &Tc, d
   {
     const double se = p.s_e, sz = p.s_zeta, sq = p.s_q;
     const double cte = 12.0 * p.theta * se * p.G * p.G, ctz = 12.0 * p.theta * sz * p.G * p.G;
-    const double k1[5] = {(1.0 - se) / 36.0, -2.0 * se / 36.0, se / 36.0,
+    const double k1[5] = {(1.0 - se) / 36.0, -2.0 * se / 36.0, 3.0 * se / 36.0,
                           (1.0 - 0.5 * se) * 6.0 / 36.0, cte / 36.0 / 9.0};
-    const double k2[5] = {(1.0 - sz) / 36.0, sz / 36.0, -sz / 36.0,
+    const double k2[5] = {(1.0 - sz) / 36.0, sz / 36.0, -3.0 * sz / 36.0,
                           -(1.0 - 0.5 * sz) * 6.0 / 36.0, -ctz / 36.0 / 9.0};
     const double kq[3] = {(1.0 - sq) / 12.0, -sq / 12.0, -(1.0 - 0.5 * sq) / 12.0};
     for (int i = 0; i < 5; i++) {

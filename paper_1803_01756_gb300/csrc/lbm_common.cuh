@@ -93,8 +93,8 @@ struct DevParams {
   float c_theta_z;        // 12 theta s_zeta G^2
   float s_e, s_z, s_q;
   // collision coefficients with the 1/D_k of M^-1 = M^T D^-1 folded in (Eqs. 7-8):
-  //   a1 = m1*/36 = k1[0] n1 + k1[1] drho + k1[2] 3rho|u|^2 + k1[3] u.F + k1[4] 9|q|^2
-  //   a2 = m2*/36 = k2[0] n2 + k2[1] drho + k2[2] 3rho|u|^2 + k2[3] u.F + k2[4] 9|q|^2
+  //   a1 = m1*/36 = k1[0] n1 + k1[1] drho + k1[2] rho|u|^2 + k1[3] u.F + k1[4] 9|q|^2
+  //   a2 = m2*/36 = k2[0] n2 + k2[1] drho + k2[2] rho|u|^2 + k2[3] u.F + k2[4] 9|q|^2
   //   a4 = m4*/12 = kq[0] n4 + kq[1] rho u_x + kq[2] F_x   (same for a6 with y)
   float k1[5], k2[5], kq[3];
   float tau_g, dtau, rho_g, inv_drho;  // Eq. 5: tau_g + clamp((rho - rho_g) inv_drho) dtau
@@ -279,15 +279,17 @@ __device__ __forceinline__ void pull_fix(const DevParams &p, int x, const StepSc
       rb = (known + p.rho_ref) / (1.0f - U);
     }
     if (unknown & (1u << 1)) g[1] = g[3] + (2.0f / 3.0f) * rb * U;
-    if (unknown & (1u << 5)) g[5] = g[7] - 0.5f * (g[2] - g[4]) + rb * U * (1.0f / 6.0f);
-    if (unknown & (1u << 8)) g[8] = g[6] + 0.5f * (g[2] - g[4]) + rb * U * (1.0f / 6.0f);
+    const float d24 = 0.5f * (g[2] - g[4]), m6 = rb * U * (1.0f / 6.0f);
+    if (unknown & (1u << 5)) g[5] = (g[7] - d24) + m6;
+    if (unknown & (1u << 8)) g[8] = (g[6] + d24) + m6;
   }
   if (x == p.nx - 1) {
     const float ro = p.rho_out;
     const float U = (g[0] + g[2] + g[4] + 2.0f * (g[1] + g[5] + g[8]) + (p.rho_ref - ro)) / ro;
     if (unknown & (1u << 3)) g[3] = g[1] - (2.0f / 3.0f) * ro * U;
-    if (unknown & (1u << 7)) g[7] = g[5] + 0.5f * (g[2] - g[4]) - ro * U * (1.0f / 6.0f);
-    if (unknown & (1u << 6)) g[6] = g[8] - 0.5f * (g[2] - g[4]) - ro * U * (1.0f / 6.0f);
+    const float d24 = 0.5f * (g[2] - g[4]), m6 = ro * U * (1.0f / 6.0f);
+    if (unknown & (1u << 7)) g[7] = (g[5] + d24) - m6;
+    if (unknown & (1u << 6)) g[6] = (g[8] - d24) - m6;
   }
 }
 
@@ -297,6 +299,16 @@ __device__ __forceinline__ void pull(const DevParams &p, const typename S::T *__
   unsigned unknown;
   pull_load<S>(p, gs, x, y, g, unknown);
   pull_fix(p, x, sc, g, unknown);
+}
+
+// rho u = sum e_i g_i + F/2 (Eq. 13; sum e_i w_i rho_ref = 0), summed in one fixed order
+// wherever a velocity is formed, so that a node's velocity has the same bits whichever
+// code path (collision or halo row) computes it
+__device__ __forceinline__ void momentum(const float g[9], float Fx, float Fy, float &jxe,
+                                         float &jye) {
+  const float d57 = g[5] - g[7], d68 = g[6] - g[8];
+  jxe = fmaf(0.5f, Fx, (g[1] - g[3]) + (d57 - d68));
+  jye = fmaf(0.5f, Fy, (g[2] - g[4]) + (d57 + d68));
 }
 
 __device__ __forceinline__ float sum9(const float g[9]) {
@@ -336,10 +348,10 @@ __device__ __forceinline__ Force interaction_force(const DevParams &p, float dps
   const float wc = psi_w_fixed > 0.0f ? p.G * p.psi_r - p.Gw * psi_w_fixed
                                       : p.wall_r - p.Gw * dpsi_c;
   Force F;
-  F.Fx = psi_c * (-p.G * qx + wc * sx);
-  F.Fy = psi_c * (-p.G * qy + wc * sy);
-  const float fx = qx - p.psi_r * sx, fy = qy - p.psi_r * sy;
-  F.fm2 = 9.0f * (fx * fx + fy * fy);
+  F.Fx = psi_c * fmaf(wc, sx, -p.G * qx);
+  F.Fy = psi_c * fmaf(wc, sy, -p.G * qy);
+  const float fx = fmaf(-p.psi_r, sx, qx), fy = fmaf(-p.psi_r, sy, qy);
+  F.fm2 = 9.0f * fmaf(fx, fx, fy * fy);
   return F;
 }
 
@@ -353,25 +365,26 @@ __device__ __forceinline__ void collide(const DevParams &p, const float g[9], fl
                                         float Fy, float fm2, float gs[9], float &rho_out,
                                         float &ux_out, float &uy_out) {
   // n = M g (Eq. 6 on deviations; m = n + rho_ref (1, -2, 1, 0, ...))
-  const float sa = g[1] + g[2] + g[3] + g[4];
-  const float sd = g[5] + g[6] + g[7] + g[8];
-  const float n1 = -4.0f * g[0] - sa + 2.0f * sd;
-  const float n2 = 4.0f * g[0] - 2.0f * sa + sd;
-  const float d57 = g[5] - g[7], d68 = g[6] - g[8];
-  const float jx = g[1] - g[3] + d57 - d68;
-  const float jy = g[2] - g[4] + d57 + d68;
-  const float n4 = -2.0f * (g[1] - g[3]) + d57 - d68;
-  const float n6 = -2.0f * (g[2] - g[4]) + d57 + d68;
-  const float n7 = g[1] - g[2] + g[3] - g[4];
-  const float n8 = g[5] - g[6] + g[7] - g[8];
+  // sums and differences of opposite directions, shared by the moments
+  const float s13 = g[1] + g[3], s24 = g[2] + g[4], s57 = g[5] + g[7], s68 = g[6] + g[8];
+  const float d13 = g[1] - g[3], d24 = g[2] - g[4], d57 = g[5] - g[7], d68 = g[6] - g[8];
+  const float sa = s13 + s24, sd = s57 + s68;
+  const float dx = d57 - d68, dy = d57 + d68;  // diagonal parts of j
+  const float n1 = fmaf(2.0f, sd, fmaf(-4.0f, g[0], -sa));
+  const float n2 = fmaf(-2.0f, sa, fmaf(4.0f, g[0], sd));
+  const float jx = d13 + dx, jy = d24 + dy;
+  const float n4 = fmaf(-2.0f, d13, dx), n6 = fmaf(-2.0f, d24, dy);
+  const float n7 = s13 - s24, n8 = s57 - s68;
 
   const float rho = p.rho_ref + drho;
   const float inv_rho = __fdividef(1.0f, rho);
-  const float ux = (jx + 0.5f * Fx) * inv_rho;  // Eq. 13
-  const float uy = (jy + 0.5f * Fy) * inv_rho;
-  const float jxe = rho * ux, jye = rho * uy;
-  const float uu3 = 3.0f * (jxe * ux + jye * uy);  // 3 rho |u|^2
-  const float uF = ux * Fx + uy * Fy;
+  float jxe, jye;  // rho u (Eq. 13)
+  momentum(g, Fx, Fy, jxe, jye);
+  const float ux = jxe * inv_rho, uy = jye * inv_rho;
+  // products are fused explicitly (fmaf) throughout, so that every copy of this code
+  // rounds the same way
+  const float uu = fmaf(jxe, ux, jye * uy);  // rho |u|^2 (the factor 3 is in k1[2], k2[2])
+  const float uF = fmaf(ux, Fx, uy * Fy);
 
   // coefficients of a7 and a8 below: 0.25 (1 - s_nu), 0.25 s_nu, 0.25 (2 - s_nu) and
   // 0.25 (1 - s_nu / 2), from the parameters when s_nu is constant
@@ -393,14 +406,17 @@ __device__ __forceinline__ void collide(const DevParams &p, const float g[9], fl
   // m* - rho_ref c, moment by moment (Eq. 7) with (1 - s/2) S from Eq. 8, each already
   // divided by its D_k: a_k = (m*_k - rho_ref c_k) / D_k
   const float a0 = drho * (1.0f / 9.0f);
-  const float a1 = p.k1[0] * n1 + p.k1[1] * drho + p.k1[2] * uu3 + p.k1[3] * uF + p.k1[4] * fm2;
-  const float a2 = p.k2[0] * n2 + p.k2[1] * drho + p.k2[2] * uu3 + p.k2[3] * uF + p.k2[4] * fm2;
+  const float a1 = fmaf(p.k1[4], fm2, fmaf(p.k1[3], uF, fmaf(p.k1[2], uu,
+                                                               fmaf(p.k1[1], drho, p.k1[0] * n1))));
+  const float a2 = fmaf(p.k2[4], fm2, fmaf(p.k2[3], uF, fmaf(p.k2[2], uu,
+                                                               fmaf(p.k2[1], drho, p.k2[0] * n2))));
   const float a3 = (jx + Fx) * (1.0f / 6.0f);
-  const float a4 = p.kq[0] * n4 + p.kq[1] * jxe + p.kq[2] * Fx;
+  const float a4 = fmaf(p.kq[2], Fx, fmaf(p.kq[1], jxe, p.kq[0] * n4));
   const float a5 = (jy + Fy) * (1.0f / 6.0f);
-  const float a6 = p.kq[0] * n6 + p.kq[1] * jye + p.kq[2] * Fy;
-  const float a7 = c7a * n7 + c7b * (jxe * ux - jye * uy) + c7c * (ux * Fx - uy * Fy);
-  const float a8 = c7a * n8 + c7b * (jxe * uy) + c8c * (ux * Fy + uy * Fx);
+  const float a6 = fmaf(p.kq[2], Fy, fmaf(p.kq[1], jye, p.kq[0] * n6));
+  const float a7 = fmaf(c7c, fmaf(ux, Fx, -(uy * Fy)),
+                        fmaf(c7b, fmaf(jxe, ux, -(jye * uy)), c7a * n7));
+  const float a8 = fmaf(c8c, fmaf(ux, Fy, uy * Fx), fmaf(c7b, jxe * uy, c7a * n8));
   // f* = M^-1 m* = M^T D^-1 m*
   const float b_ax = a0 - a1 - 2.0f * a2;   // common part of f1..f4
   const float b_dg = a0 + 2.0f * a1 + a2;   // common part of f5..f8

@@ -82,7 +82,7 @@ __device__ __forceinline__ float rk_rate(const DevParams &p, float *__restrict__
   const float lap = fmaf(-5.0f, c, fmaf(0.25f, (v5 + v7) + (v6 + v8), (v1 + v3) + (v2 + v4)));
   const float x = fmaf(c, p.inv_Tc, p.xr);  // T/Tc > 0 on fluid nodes
   const float s = x * rsqrtf(x);
-  return -(uxs * gx + uys * gy) + cl * lap - E1 * x - E2 * s;
+  return fmaf(-E2, s, fmaf(-E1, x, fmaf(cl, lap, -fmaf(uxs, gx, uys * gy))));
 }
 
 // One tile of the fused update: output columns [X0, X0 + W) and rows [Y0, ye) of
@@ -299,10 +299,10 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
               chk += ux + uy;  // rho enters at S0
             }
           } else {
-            const float jx = (fB[1] - fB[3]) + (fB[5] - fB[7]) - (fB[6] - fB[8]);
-            const float jy = (fB[2] - fB[4]) + (fB[5] - fB[7]) + (fB[6] - fB[8]);
-            ux = (jx + 0.5f * F.Fx) * inv_rho;
-            uy = (jy + 0.5f * F.Fy) * inv_rho;
+            float jxe, jye;
+            momentum(fB, F.Fx, F.Fy, jxe, jye);
+            ux = jxe * inv_rho;
+            uy = jye * inv_rho;
           }
           if (TH) {
             // the velocity inlet's ghost holds the inlet velocity; with a pressure inlet
@@ -313,7 +313,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
             if (mirror_in) F2(ring_u, sl - 4) = uu;
             // energy coefficients of the node (see rk_rate): cl, E1 / (3 div u), E2 / (3 div u)
             const float br = p.eos_b * rho;
-            const float z = __fdividef(p.akap1_cv3 * rho, 1.0f + 2.0f * br - br * br);
+            const float z = __fdividef(p.akap1_cv3 * rho, fmaf(br, 2.0f - br, 1.0f));
             F4(ring_cf, sl) = make_float4(p.lam23_cv * inv_rho,
                                       __fdividef(p.RTc_cv3, 1.0f - br) - p.kappa_r * z, z, 0.0f);
           }
