@@ -39,11 +39,19 @@ SPLIT_KERNEL_BYTES = {"k_density_psi": 36 + 4 + 8, "k_collide": 36 + 4 + 36 + 8,
 L2_BYTES = 129e6
 # updates per CUDA-graph chunk of lbm_step on the fused path
 GRAPH_CHUNK = 16
+# maximum SM clock of the GB300 (nvidia-smi clocks.max.sm)
+SM_MAX_MHZ = 2070
 # DRAM bytes (read + write) of one k_fused_step launch on the 4096 x 512 channel with
 # FP32 storage, measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch); reported only for that kernel, workload and storage.  Re-measure whenever the
 # kernel changes.
-FUSED_F32_4096x512_DRAM_BYTES = 109.522176e6 + 40.404480e6
+FUSED_F32_4096x512_DRAM_BYTES = 109.568768e6 + 40.951296e6
+# Warp instructions of one k_fused_step launch on the same workload and storage (ncu
+# smsp__inst_executed.sum); with the live launch time it gives the kernel's instruction
+# issue rate against the SMs' issue limit (4 schedulers x 1 warp instruction per cycle
+# each at the maximum SM clock), the limit this kernel is bound by.  Re-measure whenever
+# the kernel changes.
+FUSED_F32_4096x512_WARP_INSTR = 52073788
 
 
 # --physics: which parts of the update run (the energy equation of Eqs. 16-18 and the
@@ -288,6 +296,17 @@ def our_arm(args, world, rank, local, dist):
                                   f"{args.steps} updates"),
                 "event_bracketed_launch_us": top_ms / top_n * 1e3,
                 "kernel_share": shares}
+    if traffic is not None and args.traffic is None:
+        # the same kernel, workload and storage as the ncu counts: its issue roofline
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = (clocks or {}).get("sm_max_mhz") or SM_MAX_MHZ
+        issue_peak = sms * 4 * mhz * 1e6
+        issue = FUSED_F32_4096x512_WARP_INSTR / (avg_us / 1e6)
+        roofline["issue"] = {
+            "achieved": issue / 1e9, "peak": issue_peak / 1e9, "unit": "G warp-instr/s",
+            "frac": issue / issue_peak,
+            "instr_per_cell_update": FUSED_F32_4096x512_WARP_INSTR * 32 / cells,
+            "peak_source": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz"}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
