@@ -131,8 +131,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
   // written one row step earlier, at the bottom row 0 writes its value into the slot of
   // row -1 (not read by any stage before then).  Adiabatic columns come with periodic x.
   const float twall = wall_T_dev(pg, cx), twall_top = wall_T_top_dev(pg, cx);
-  const bool adi_bot = YW && pg.adiabatic && wall_adiabatic(pg, cx, false);
-  const bool adi_top = YW && pg.adiabatic && wall_adiabatic(pg, cx, true);
+  // (lbm_create accepts adiabatic columns only with periodic x: compile-time false for open x)
+  const bool adi_bot = YW && !XO && pg.adiabatic && wall_adiabatic(pg, cx, false);
+  const bool adi_top = YW && !XO && pg.adiabatic && wall_adiabatic(pg, cx, true);
 
   // Pull offsets relative to the node's own index (Eq. 12, f_i(x) = f*_i(x - e_i)), used
   // on every row not next to a wall.  Next to a periodic seam the source column wraps;
