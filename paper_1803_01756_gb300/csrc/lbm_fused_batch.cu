@@ -8,8 +8,9 @@ namespace {
 
 // Persistent batched update: resident CTAs take tiles of many lattices from one
 // work-list (largest lattices first), so uneven lattice sizes balance across the SMs.
-// Block b starts with tile b (consecutive blocks sit on different SMs, so a batch with
-// fewer tiles than SMs runs one tile per SM); later tiles come from an atomic counter.
+// Block b starts with tile b (a batch with fewer tiles than resident CTAs is launched with
+// one CTA per tile, which the hardware spreads over the SMs); later tiles come from an
+// atomic counter.
 // The last CTA to leave resets the counters.
 // (Reading the bulk physics from a constant-bank copy when all lattices share it
 // measured 2 % faster than the shared-memory copy used here, and a kernel holding
