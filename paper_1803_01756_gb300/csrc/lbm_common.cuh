@@ -193,12 +193,12 @@ __device__ __forceinline__ float pseudopotential_dev(const DevParams &p, float d
   const float tA = invD * fmaf(p.ps_phi * ds * (r + p.rphi_r), rho * rho, p.ps_B * drho * g);
   const float dpsi2 = fmaf(p.ps_3, drho, tR - tA);
   const float psi2 = p.psi_r2 + dpsi2;
-  if (!(psi2 >= 0.0f)) {
-    st |= ST_PSI_NEG;
-    return -p.psi_r;  // psi = 0
-  }
-  const float den = sqrtf(psi2) + p.psi_r;
-  return den > 0.0f ? __fdividef(dpsi2, den) : 0.0f;
+  // a negative argument gives psi = 0 and a status bit (selects, no branch)
+  const bool neg = !(psi2 >= 0.0f);
+  st |= neg ? ST_PSI_NEG : 0u;
+  const float den = sqrtf(fmaxf(psi2, 0.0f)) + p.psi_r;
+  const float d = den > 0.0f ? __fdividef(dpsi2, den) : 0.0f;
+  return neg ? -p.psi_r : d;
 }
 
 // ---------------------------------------------------------------------------

@@ -125,6 +125,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
   const bool mirror = XO && c == pg.nx - 1 && t + 1 < FNT;
   const bool mirror_in0 = XO && c == 0 && t >= 1;
   const bool mirror_in = mirror_in0 && pg.p_inlet;
+  // the CTA holds a column of an open end (uniform over the CTA): only such CTAs have
+  // Zou-He unknowns to fix
+  const bool xb = XO && (c - t <= 0 || c - t + FNT - 1 >= pg.nx - 1);
   // Energy-equation ghosts of the walls (Section 3.2): isothermal columns hold the wall
   // temperature of their wall; on adiabatic columns every stage field's ghost copies the
   // fluid node across the wall: at the top the ghost row takes the value of row ny - 1
@@ -426,7 +429,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
         F1(ring_T, sT) = r < 0 ? twall : (adi_top ? F1(ring_T, R8(1)) : twall_top);
         F1(ring_psi, sl) = 0.0f;
       } else {
-        pull_fix(pg, cx, sc, fc, unk);
+        if (xb) pull_fix(pg, cx, sc, fc, unk);
         float dpsi = 0.0f;
         const float drho = sum9(fc);
         drhoC = drho;
