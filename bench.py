@@ -45,7 +45,7 @@ SM_MAX_MHZ = 2070
 # FP32 storage, measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch); reported only for that kernel, workload and storage.  Re-measure whenever the
 # kernel changes.
-FUSED_F32_4096x512_DRAM_BYTES = 109.515776e6 + 40.280320e6
+FUSED_F32_4096x512_DRAM_BYTES = 109.472256e6 + 40.730368e6
 # Warp instructions of one k_fused_step launch on the same workload and storage (ncu
 # smsp__inst_executed.sum); with the live launch time it gives the kernel's instruction
 # issue rate against the SMs' issue limit (4 schedulers x 1 warp instruction per cycle
