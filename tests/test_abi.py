@@ -109,3 +109,46 @@ def test_invalid_arguments_are_rejected(lib, nx, ny, over):
     with pytest.raises(LbmError) as ei:
         Lattice(nx, ny, inputs.base_params(**over))
     assert ei.value.code == -1  # LBM_ERR_ARG
+
+
+def test_null_handles_are_rejected_before_any_device_call(lib):
+    """Every entry point that takes a handle returns LBM_ERR_ARG for a null one (the
+    destroy calls do nothing), without touching the device: this runs without a GPU."""
+    from paper_1803_01756_gb300 import lattice
+    L = lattice.load_library()
+    n = None
+    d = ctypes.c_double()
+    u = ctypes.c_uint()
+    z = ctypes.c_size_t()
+    i = ctypes.c_int()
+    lg = ctypes.c_long()
+    info = lattice.LbmInfo()
+    p = lattice.make_params({})
+    calls = {
+        "lbm_write_fields": lambda: L.lbm_write_fields(n, None, None, n),
+        "lbm_step": lambda: L.lbm_step(n, 1, n),
+        "lbm_set_graph": lambda: L.lbm_set_graph(n, 1),
+        "lbm_status": lambda: L.lbm_status(n, ctypes.byref(u), 0, n),
+        "lbm_read_fields": lambda: L.lbm_read_fields(n, None, None, None, None, n),
+        "lbm_reduce": lambda: L.lbm_reduce(n, ctypes.byref(d), ctypes.byref(d), n),
+        "lbm_state_bytes": lambda: L.lbm_state_bytes(n, ctypes.byref(z)),
+        "lbm_read_state": lambda: L.lbm_read_state(n, None, 0, n),
+        "lbm_write_state": lambda: L.lbm_write_state(n, None, 0, n),
+        "lbm_info": lambda: L.lbm_info(n, ctypes.byref(info)),
+        "lbm_timing_enable": lambda: L.lbm_timing_enable(n, 1),
+        "lbm_timing_get": lambda: L.lbm_timing_get(n, None, None, None, 0, ctypes.byref(i), n),
+        "lbm_batch_create": lambda: L.lbm_batch_create(None, 0, ctypes.byref(ctypes.c_void_p())),
+        "lbm_batch_step": lambda: L.lbm_batch_step(n, 1, n),
+        "lbm_batch_set_graph": lambda: L.lbm_batch_set_graph(n, 1),
+        "lbm_batch_set_tile_rows": lambda: L.lbm_batch_set_tile_rows(n, 16),
+        "lbm_batch_autotune": lambda: L.lbm_batch_autotune(n, 4, ctypes.byref(i), n),
+        "lbm_batch_info": lambda: L.lbm_batch_info(n, None, None, None),
+        "lbm_submit": lambda: L.lbm_submit(n, 8, 8, ctypes.byref(p), None, 1, ctypes.byref(lg)),
+        "lbm_poll": lambda: L.lbm_poll(n, 0, ctypes.byref(i), None, None, None, None, None),
+        "lbm_wait": lambda: L.lbm_wait(n, 0, 0.0, ctypes.byref(i)),
+        "lbm_server_stats": lambda: L.lbm_server_stats(n, None),
+    }
+    for name, call in calls.items():
+        assert call() == -1, name
+    L.lbm_batch_destroy(n)
+    L.lbm_server_destroy(n)
