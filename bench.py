@@ -41,17 +41,32 @@ L2_BYTES = 129e6
 GRAPH_CHUNK = 16
 # maximum SM clock of the GB300 (nvidia-smi clocks.max.sm)
 SM_MAX_MHZ = 2070
-# DRAM bytes (read + write) of one k_fused_step launch on the 4096 x 512 channel with
-# FP32 storage, measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
-# launch); reported only for that kernel, workload and storage.  Re-measure whenever the
-# kernel changes.
+# ncu counters of one k_fused_step launch on the 4096 x 512 channel with FP32 storage:
+# DRAM bytes read + written (dram__bytes_read.sum + dram__bytes_write.sum) and warp
+# instructions executed (smsp__inst_executed.sum; with the live launch time they give the
+# kernel's issue rate against the SMs' issue limit of 4 schedulers x 1 warp instruction per
+# cycle).  They hold for the kernel sources whose hash is FUSED_COUNTERS_SOURCE (the
+# profiles/ summary of the capture records the same hash); when the built sources hash
+# differently the counters are stale and the bench reports them as null.
 FUSED_F32_4096x512_DRAM_BYTES = 109.472256e6 + 40.730368e6
-# Warp instructions of one k_fused_step launch on the same workload and storage (ncu
-# smsp__inst_executed.sum); with the live launch time it gives the kernel's instruction
-# issue rate against the SMs' issue limit (4 schedulers x 1 warp instruction per cycle
-# each at the maximum SM clock), the limit this kernel is bound by.  Re-measure whenever
-# the kernel changes.
 FUSED_F32_4096x512_WARP_INSTR = 51726868
+FUSED_COUNTERS_SOURCE = "6cd08d5f1fc51832"
+# the files that determine the fused kernel's machine code
+FUSED_SOURCES = ["paper_1803_01756_gb300/csrc/lbm_common.cuh",
+                 "paper_1803_01756_gb300/csrc/lbm_internal.h",
+                 "paper_1803_01756_gb300/csrc/lbm_fused_tile.cuh",
+                 "paper_1803_01756_gb300/csrc/lbm_fused.cu",
+                 "paper_1803_01756_gb300/build.py"]
+
+
+def fused_source_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the fused kernel's source files."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in FUSED_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 # --physics: which parts of the update run (the energy equation of Eqs. 16-18 and the
@@ -191,7 +206,7 @@ def reference_arm(args, world, rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "nx": nx, "ny": ny, "sample_of": [w["nx"], w["ny"]]},
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host_nproc": os.cpu_count()},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -210,7 +225,8 @@ def our_arm(args, world, rank, local, dist):
     # parts of the update switched off (to see what each part costs); the default is all
     w["params"] = dict(w["params"], **PHYSICS[args.physics])
     nx, ny = w["nx"], w["ny"]
-    kernel = {"auto": L.KERNEL_AUTO, "split": L.KERNEL_SPLIT, "fused": L.KERNEL_FUSED}[args.kernel]
+    kernel = {"auto": L.KERNEL_AUTO, "split": L.KERNEL_SPLIT, "fused": L.KERNEL_FUSED,
+              "fused1": L.KERNEL_FUSED_1COL, "fused2": L.KERNEL_FUSED_2COL}[args.kernel]
     storage = {"f32": 0, "bf16": 1, "f16": 2}[args.storage]
     # algorithmic bytes per cell-update: populations read and written once, T read and written
     bytes_cell = 2 * 9 * (4 if args.storage == "f32" else 2) + 8
@@ -222,7 +238,9 @@ def our_arm(args, world, rank, local, dist):
         steps = args.cpu_steps
         mlups, dt = time_oracle(w, nx, ny, steps)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"{steps} updates of the full {nx}x{ny} channel ({dt:.1f} s, 1 thread)"}
+               "sample": f"{steps} updates of the full {nx}x{ny} channel ({dt:.1f} s, 1 thread)",
+               "host_nproc": os.cpu_count(),
+               "note": "the oracle is a sequential program and runs on one of the host's cores"}
 
     stream = torch.cuda.current_stream()
     lat = L.Lattice(nx, ny, w["params"], kernel=kernel, storage=storage)
@@ -235,8 +253,10 @@ def our_arm(args, world, rank, local, dist):
     lat.step(GRAPH_CHUNK, stream=stream)
     torch.cuda.synchronize()
 
-    # ---- timed region: K updates, device time from CUDA events on the stream ----
-    # (the fused path replays 16-update CUDA graphs here)
+    # ---- timed region: K updates, device time from CUDA events on the stream, with a
+    # device synchronize on both sides; repeated (K updates each time) until the repeats
+    # add up to --min-timed-s, so that the clock sampler sees the GPU under load, and the
+    # median repeat is reported (the fused path replays 16-update CUDA graphs here) ----
     sampler = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -244,13 +264,19 @@ def our_arm(args, world, rank, local, dist):
     sampler.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    lat.step(args.steps, stream=stream)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    repeats = []
+    while True:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        lat.step(args.steps, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        repeats.append(ev0.elapsed_time(ev1))
+        if sum(repeats) >= 1e3 * args.min_timed_s or len(repeats) >= 100000:
+            break
     if dist:
         dist.barrier()
-    elapsed_ms = ev0.elapsed_time(ev1)
+    elapsed_ms = statistics.median(repeats)
     # ---- per-kernel launch durations: a second pass of K updates with CUDA events
     # recorded around every launch on the stream (one launch per kernel and update) ----
     lat.timing_enable(True)
@@ -281,8 +307,11 @@ def our_arm(args, world, rank, local, dist):
     top_ms, top_n = per_kernel[top_name]
     per_cell = bytes_cell if top_name == "k_fused_step" else SPLIT_KERNEL_BYTES[top_name]
     traffic = args.traffic
+    src_hash = fused_source_hash()
+    counters_current = src_hash == FUSED_COUNTERS_SOURCE
     if (traffic is None and top_name == "k_fused_step" and args.storage == "f32"
-            and args.workload == "channel_4096x512" and args.physics == "full"):
+            and args.workload == "channel_4096x512" and args.physics == "full"
+            and counters_current):
         traffic = FUSED_F32_4096x512_DRAM_BYTES
     bytes_per_launch = per_cell * cells
     avg_us = elapsed_ms * shares[top_name] / top_n * 1e3
@@ -295,7 +324,8 @@ def our_arm(args, world, rank, local, dist):
                                   f"CUDA events around each launch in a second pass of "
                                   f"{args.steps} updates"),
                 "event_bracketed_launch_us": top_ms / top_n * 1e3,
-                "kernel_share": shares}
+                "kernel_share": shares, "kernel_source_sha": src_hash,
+                "counters_source_sha": FUSED_COUNTERS_SOURCE}
     if traffic is not None and args.traffic is None:
         # the same kernel, workload and storage as the ncu counts: its issue roofline
         sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -354,8 +384,13 @@ def our_arm(args, world, rank, local, dist):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "nx": nx, "ny": ny, "storage": args.storage,
                    "physics": args.physics,
+                   "timing": (f"median of {len(repeats)} timed regions of {args.steps} updates "
+                              f"each ({sum(repeats) / 1e3:.2f} s in all; min "
+                              f"{min(repeats) / args.steps * 1e3:.2f}, max "
+                              f"{max(repeats) / args.steps * 1e3:.2f} us per update)"),
                    "kernel": {1: "split", 2: "fused"}[info["kernel"]],
                    "tile": [info["tile_cols"], info["tile_rows"]],
+                   "cols_per_thread": info["cols_per_thread"],
                    "launch": ("16-update CUDA graphs" if info["kernel"] == L.KERNEL_FUSED
                               else "one launch per kernel"),
                    "untimed_updates_before": args.warmup + GRAPH_CHUNK,
@@ -455,15 +490,12 @@ def serving_jobs(n: int, steps: int, seed: int = 4):
     return jobs
 
 
-def serving_arm(args):
-    """jobs/hour and latency of the continuous-batching server (BF16 storage) against
-    the same arrivals solved one at a time in FP32 (first come, first served)."""
+def run_server(args, L, jobs, rho0, storage):
+    """Serve the job stream with the given population storage: Poisson arrivals from a
+    client thread, continuous batching in the library's worker.  Returns (wall seconds,
+    per-job latencies, peak device bytes)."""
     import threading
     import torch
-    from paper_1803_01756_gb300 import lattice as L
-    torch.cuda.set_device(0)
-    jobs = serving_jobs(args.jobs, args.job_steps)
-    rho0 = [inputs.noisy_density(j["nx"], j["ny"], inputs.RHO_V_086, 0.01, j["seed"]) for j in jobs]
     free, _ = torch.cuda.mem_get_info()
     srv = L.Server(hbm_budget=int(0.5 * free), max_active=args.max_active,
                    chunk_steps=args.chunk_steps)
@@ -475,7 +507,7 @@ def serving_arm(args):
             delay = t0 + j["t"] - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            ids[k] = srv.submit(j["nx"], j["ny"], j["p"], j["steps"], rho0[k], storage=1)
+            ids[k] = srv.submit(j["nx"], j["ny"], j["p"], j["steps"], rho0[k], storage=storage)
 
     th = threading.Thread(target=client)
     th.start()
@@ -487,6 +519,25 @@ def serving_arm(args):
     wall = time.perf_counter() - t0
     peak = srv.stats()["peak_bytes"]
     srv.close()
+    return wall, lat, peak
+
+
+def serving_arm(args):
+    """jobs/hour and latency of the continuous-batching server, with BF16 population
+    storage (the headline) and with FP32 storage (the batching gain alone), against the
+    same arrivals solved one at a time in FP32 (first come, first served)."""
+    import torch
+    from paper_1803_01756_gb300 import lattice as L
+    torch.cuda.set_device(0)
+    jobs = serving_jobs(args.jobs, args.job_steps)
+    rho0 = [inputs.noisy_density(j["nx"], j["ny"], inputs.RHO_V_086, 0.01, j["seed"]) for j in jobs]
+    cells = sum(j["nx"] * j["ny"] * j["steps"] for j in jobs)
+    served = {}
+    for name, storage in (("bf16", 1), ("f32", 0)):
+        wall, lat, peak = run_server(args, L, jobs, rho0, storage)
+        served[name] = {"jobs_per_hour": len(jobs) / wall * 3600, "wall_s": wall,
+                        "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                        "mlups": cells / wall / 1e6, "peak_device_bytes": peak}
     # sequential FP32 solves of the same stream, one at a time
     service = []
     for k, j in enumerate(jobs):
@@ -503,18 +554,20 @@ def serving_arm(args):
         start = max(finish, j["t"])
         finish = start + sv
         seq_lat.append(finish - j["t"])
-    cells = sum(j["nx"] * j["ny"] * j["steps"] for j in jobs)
+    head = served["bf16"]
     line = {
-        "metric": "jobs/hour (continuous-batching server)", "value": len(jobs) / wall * 3600,
+        "metric": "jobs/hour (continuous-batching server)", "value": head["jobs_per_hour"],
         "unit": "jobs/h", "n_gpus": 1, "steps": len(jobs), "warmup": 0,
-        "ms_per_step": wall / len(jobs) * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "ms_per_step": head["wall_s"] / len(jobs) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
         "config": {"workload": "serving: Poisson 20 jobs/s, 90 % 256-2048 x 32-256 channels, "
                                "10 % 4096x512", "jobs": len(jobs), "steps_per_job": args.job_steps,
-                   "storage": "bf16", "chunk_steps": args.chunk_steps,
-                   "max_active": args.max_active, "peak_device_bytes": peak},
-        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-        "mlups": cells / wall / 1e6,
+                   "storage": "bf16", "arithmetic": "f32", "chunk_steps": args.chunk_steps,
+                   "max_active": args.max_active, "peak_device_bytes": head["peak_device_bytes"]},
+        "latency_s": {"p50": head["p50"], "p99": head["p99"]},
+        "mlups": head["mlups"],
+        "server_fp32": served["f32"],
         "sequential_fp32": {"jobs_per_hour": len(jobs) / finish * 3600,
                             "p50": float(np.percentile(seq_lat, 50)),
                             "p99": float(np.percentile(seq_lat, 99)),
@@ -530,12 +583,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="channel_4096x512", choices=sorted(inputs.WORKLOADS))
-    ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused", "fused1", "fused2"],
+                    help="fused1 / fused2: the fused kernel with one / two lattice columns per thread")
     ap.add_argument("--physics", default="full", choices=sorted(PHYSICS),
                     help="full update, or without the energy equation / the pseudopotential")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="population storage (FP32 arithmetic in every case)")
     ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--min-timed-s", type=float, default=2.0,
+                    help="repeat the K-update timed region until the repeats add up to this")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-inner", type=int, default=100)

@@ -54,7 +54,9 @@ extern "C" {
 
 #define LBM_KERNEL_AUTO 0
 #define LBM_KERNEL_SPLIT 1   /* density/psi, collide, energy: three launches per update */
-#define LBM_KERNEL_FUSED 2   /* one launch per update */
+#define LBM_KERNEL_FUSED 2   /* one launch per update; the library picks the columns per thread */
+#define LBM_KERNEL_FUSED_1COL 3 /* the fused kernel with one lattice column per thread */
+#define LBM_KERNEL_FUSED_2COL 4 /* the fused kernel with two lattice columns per thread */
 
 /* Problem parameters, copied by value at lbm_create (the caller keeps ownership). */
 typedef struct lbm_params {
@@ -100,6 +102,8 @@ typedef struct lbm_info {
   int kernel;                 /* kernel path in use (LBM_KERNEL_SPLIT or _FUSED) */
   int tile_cols, tile_rows;   /* fused kernel: most output columns and rows of one CTA's tile
                                  (0 on the split path) */
+  int cols_per_thread;        /* fused kernel: lattice columns each thread sweeps (1 or 2;
+                                 0 on the split path) */
 } lbm_info_t;
 
 /* Create a lattice of nx * ny nodes with parameters *p.  Allocates all device
@@ -138,18 +142,36 @@ int lbm_set_graph(lbm_h h, int enable);
    stream.  Returns LBM_ERR_UNSTABLE if device status bits are set (fields still written). */
 int lbm_read_fields(lbm_h h, double *rho, double *ux, double *uy, double *T, void *stream);
 
-/* FP64 sums over all nodes of rho and rho Cv T at the current time.  Synchronises. */
+/* FP64 sums over all nodes of rho (the density of Eq. 13, sum_i f_i) and of rho Cv T
+   (the internal energy per unit volume whose balance Eq. 16 states) at the current time:
+   *mass and *heat (either may be NULL).  The per-node values are formed in FP32 on the
+   device and summed in FP64 (warp shuffles, then one pass over per-block partials).
+   Synchronises the stream; LBM_ERR_CUDA if a launch or copy fails. */
 int lbm_reduce(lbm_h h, double *mass, double *heat, void *stream);
 
 /* Device status bits (LBM_ST_*) accumulated since creation; clears them when clear != 0.
-   Synchronises the stream. */
+   The bits flag states outside the domain of the model's equations: a negative argument of
+   the square root of Eq. 10, b rho at or beyond the pole of Eq. 11, rho <= 0 (Eq. 13 divides
+   by it), T <= 0 (the sqrt(T/Tc) of Eq. 11 and the RK4 stages of Eqs. 16-18), or a NaN.
+   *bits written on return.  Synchronises the stream; LBM_ERR_ARG for NULL pointers. */
 int lbm_status(lbm_h h, unsigned *bits, int clear, void *stream);
 
-/* Checkpoint: the populations, temperature and time as an opaque byte string. */
+/* Checkpoint of the complete state of the update (Eqs. 1-18 advance the populations f_i of
+   Eq. 1 and the temperature of Eq. 16; every other field is recomputed from them): the stored
+   post-collision populations, the temperature and the time t as one opaque byte string of
+   lbm_state_bytes() bytes (a header with the sizes, pitch, storage and t, then the device
+   arrays as stored).  The caller owns buf.  lbm_read_state copies the current state out;
+   lbm_write_state restores it into a handle of the same nx, ny and storage, after which
+   lbm_step continues bit for bit as the original would.  Both synchronise the stream.
+   LBM_ERR_ARG for NULL pointers or a buffer smaller than lbm_state_bytes() on read;
+   LBM_ERR_STATE for a short or foreign byte string on write. */
 int lbm_state_bytes(lbm_h h, size_t *bytes);
 int lbm_read_state(lbm_h h, void *buf, size_t bytes, void *stream);
 int lbm_write_state(lbm_h h, const void *buf, size_t bytes, void *stream);
 
+/* Sizes, time, the critical temperature of Eq. 11 and the deviation references of the
+   handle, its device footprint and kernel tiling, written to the caller's *info.  Host
+   only (no device call).  LBM_ERR_ARG for NULL pointers. */
 int lbm_info(lbm_h h, lbm_info_t *info);
 
 /* Per-kernel CUDA-event timing of lbm_step launches.  enable != 0 starts recording
@@ -167,6 +189,35 @@ const char *lbm_strerror(int code);
 
 /* Critical temperature of Eq. 11 for the given parameters. */
 double lbm_critical_temperature(const lbm_params_t *p);
+
+/* Density that the pressure inlet (Section 3.3, LBM_X_PRESSURE_INLET) imposes on column 0
+   at time t: the root on the vapour branch of the Peng-Robinson isotherm (Eq. 11) at
+   T_inlet of P(rho) = p0 (1 + p_amp_frac sin(2 pi t / u_period)), p0 = P(rho_out, T_inlet);
+   the vapour branch runs from 0 to the isotherm's first maximum (to 0.999 / b above Tc),
+   and a target above its top pressure gives the branch end.  Host-only: no device call,
+   usable without a GPU.  *rho written in FP64.  LBM_ERR_ARG for NULL pointers or
+   parameters outside the ranges lbm_create accepts for this inlet. */
+int lbm_pressure_inlet_density(const lbm_params_t *p, long long t, double *rho);
+
+/* Droplet statistics of a density field (the condensate on the channel walls of Section 3.3,
+   whose droplet count and spacing the paper's closing wettability discussion compares).
+   Liquid nodes have rho > threshold (for example the mean of the coexistence densities);
+   droplets are 8-connected liquid components that touch a wall row (y = 0: bottom, y = ny - 1:
+   top; a component touching both counts for both); a droplet's position is the mean x of its
+   nodes (the circular mean when x is periodic).  rho: host [ny][nx] doubles, caller-owned.
+   Host-only (no device call, usable without a GPU).  LBM_ERR_ARG for NULL pointers, sizes
+   outside [1, 2^20] or a NaN threshold. */
+typedef struct lbm_droplet_stats {
+  int count[2];            /* droplets on the bottom and on the top wall */
+  double spacing[2];       /* mean x distance between neighbouring droplet positions on each wall,
+                              (last - first) / (count - 1); nx / count with periodic x; 0 for
+                              fewer than two droplets */
+  double condensed_mass;   /* sum over liquid nodes of (rho - rho_v) */
+  long long liquid_nodes;  /* nodes with rho > threshold */
+  int detached;            /* liquid components touching neither wall */
+} lbm_droplet_stats_t;
+int lbm_droplet_stats(const double *rho, int nx, int ny, double threshold, double rho_v,
+                      int periodic_x, lbm_droplet_stats_t *out);
 
 /* ---- batched updates of many lattices (one persistent launch per step) ----
    A batch groups lattices that share the boundary modes (x_bc class, y_bc), the

@@ -24,7 +24,7 @@ LIB = os.path.join(BUILD, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 _FAST = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
-PER_FILE = {"lbm_fused.cu": _FAST, "lbm_fused_batch.cu": _FAST}
+PER_FILE = {"lbm_fused.cu": _FAST, "lbm_fused_c2.cu": _FAST, "lbm_fused_batch.cu": _FAST}
 _lock = threading.Lock()
 
 

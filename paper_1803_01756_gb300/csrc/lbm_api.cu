@@ -52,6 +52,13 @@ double critical_temperature(const lbm_params_t &p) {
 
 bool valid_rate(double s) { return s > 0.0 && s < 2.0; }
 
+// Lattice columns per thread of the fused kernel for an nx x ny lattice.
+int default_cpt(int nx, int ny) {
+  (void)nx;
+  (void)ny;
+  return 1;
+}
+
 int validate(int nx, int ny, const lbm_params_t &p) {
   if (nx < 1 || ny < 1) return LBM_ERR_ARG;
   if (nx > (1 << 20) || ny > (1 << 20)) return LBM_ERR_ARG;
@@ -68,7 +75,7 @@ int validate(int nx, int ny, const lbm_params_t &p) {
   if (!valid_rate(p.s_e) || !valid_rate(p.s_zeta) || !valid_rate(p.s_q)) return LBM_ERR_ARG;
   if (p.storage != LBM_STORAGE_F32 && p.storage != LBM_STORAGE_BF16 && p.storage != LBM_STORAGE_F16)
     return LBM_ERR_ARG;
-  if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_FUSED) return LBM_ERR_ARG;
+  if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_FUSED_2COL) return LBM_ERR_ARG;
   if (p.u_period < 0.0 || std::fabs(p.u_amp) >= 1.0) return LBM_ERR_ARG;
   // adiabatic wall columns (outside a non-empty isothermal window) only with periodic x
   const bool adia = (p.top_iso_x1 > p.top_iso_x0 && (p.top_iso_x0 > 0 || p.top_iso_x1 < nx)) ||
@@ -211,41 +218,114 @@ double host_pressure(const lbm_params_t &p, double Tc, double rho, double T) {
   return rho * p.eos_R * T / (1.0 - br) - p.eos_a * r * r * rho * rho / (1.0 + 2.0 * br - br * br);
 }
 
-// Upper end of the vapour branch at temperature T: the first density where the isotherm
-// stops rising (its first maximum), or close to the pole when it rises throughout.
-double vapour_branch_end(const lbm_params_t &p, double Tc, double T) {
-  const double rmax = 0.999 / p.eos_b, h = 1e-7;
-  auto rising = [&](double r) {
-    return host_pressure(p, Tc, r + h, T) - host_pressure(p, Tc, r - h, T) > 0.0;
+// Real roots of the polynomial c[0] + c[1] x + ... + c[deg] x^deg in [lo, hi], in
+// increasing order.  The roots of the derivative (found the same way, down to degree 1)
+// split [lo, hi] into pieces on which the polynomial is monotone, so each piece holds at
+// most one root, located by Newton steps kept inside the piece's bracket.
+int poly_roots(const double *c, int deg, double lo, double hi, double *out) {
+  auto eval = [&](double x) {
+    double v = c[deg];
+    for (int k = deg - 1; k >= 0; k--) v = v * x + c[k];
+    return v;
   };
-  double prev = 1e-6;
-  for (double r = prev + 1e-3; r < rmax; r += 1e-3) {
-    if (!rising(r)) {
-      double lo = prev, hi = r;
-      for (int it = 0; it < 100; it++) {
-        const double mid = 0.5 * (lo + hi);
-        if (rising(mid)) lo = mid; else hi = mid;
-      }
-      return lo;
+  while (deg > 0 && c[deg] == 0.0) deg--;
+  if (deg == 0) return 0;
+  if (deg == 1) {
+    const double x = -c[0] / c[1];
+    if (x >= lo && x <= hi) {
+      out[0] = x;
+      return 1;
     }
-    prev = r;
+    return 0;
   }
-  return rmax;
+  double dc[4], crit[4];
+  for (int k = 1; k <= deg; k++) dc[k - 1] = k * c[k];
+  const int nc = poly_roots(dc, deg - 1, lo, hi, crit);
+  double edge[6];
+  int ne = 0;
+  edge[ne++] = lo;
+  for (int k = 0; k < nc; k++) edge[ne++] = crit[k];
+  edge[ne++] = hi;
+  int n = 0;
+  for (int k = 0; k + 1 < ne; k++) {
+    double a = edge[k], b = edge[k + 1];
+    double fa = eval(a), fb = eval(b);
+    if (fa == 0.0) {
+      if (n == 0 || out[n - 1] != a) out[n++] = a;
+      continue;
+    }
+    if (fa * fb > 0.0) continue;
+    if (fb == 0.0) continue;  // taken as the left end of the next piece
+    double x = 0.5 * (a + b);
+    for (int it = 0; it < 200; it++) {
+      const double fx = eval(x);
+      if (fx == 0.0) break;
+      if ((fx > 0.0) == (fa > 0.0)) { a = x; fa = fx; } else { b = x; }
+      double d = dc[deg - 1];
+      for (int m = deg - 2; m >= 0; m--) d = d * x + dc[m];
+      double xn = d != 0.0 ? x - fx / d : 0.5 * (a + b);
+      if (!(xn > a && xn < b)) xn = 0.5 * (a + b);
+      if (std::fabs(xn - x) <= 1e-16 * std::fabs(x) || b - a <= 1e-16 * std::fabs(b)) {
+        x = xn;
+        break;
+      }
+      x = xn;
+    }
+    out[n++] = x;
+  }
+  return n;
 }
 
-// inlet density of the pressure inlet at time t (bisection on the vapour branch)
-double inlet_density(const lbm_lattice *h, long long t) {
-  const lbm_params_t &p = h->p;
-  const double T = h->Tc * p.T_inlet;
-  const double p0 = host_pressure(p, h->Tc, p.rho_out, T);
+// Upper end of the vapour branch of the Peng-Robinson isotherm (Eq. 11) at temperature T:
+// its first maximum, where dP/drho = R T / (1 - b rho)^2 - 2 a phi rho (1 + b rho) / D^2
+// vanishes (D = 1 + 2 b rho - b^2 rho^2), or 0.999 / b when the isotherm rises up to the
+// pole (T >= Tc).  With x = b rho, dP/drho has the sign of the quartic
+//   q(x) = D^2 - c x (1 + x) (1 - x)^2
+//        = 1 + (4 - c) x + (2 + c) x^2 + (c - 4) x^3 + (1 - c) x^4,   c = 2 a phi / (b R T),
+// and q(0) = 1 > 0, so the branch ends at the smallest root of q in (0, 1).
+double vapour_branch_end(const lbm_params_t &p, double Tc, double T) {
+  const double k = 0.37464 + 1.54226 * p.eos_omega - 0.26992 * p.eos_omega * p.eos_omega;
+  const double r = 1.0 + k * (1.0 - std::sqrt(T / Tc));
+  const double c = 2.0 * p.eos_a * r * r / (p.eos_b * p.eos_R * T);
+  const double q[5] = {1.0, 4.0 - c, 2.0 + c, c - 4.0, 1.0 - c};
+  double roots[4];
+  const int n = poly_roots(q, 4, 0.0, 0.999, roots);
+  return (n > 0 ? roots[0] : 0.999) / p.eos_b;
+}
+
+// Inlet density of the pressure inlet at time t: the density on the vapour branch whose
+// pressure is p0 (1 + p_amp_frac sin(2 pi t / P)), p0 = P(rho_out, T_inlet).  P rises
+// strictly on [0, branch end], so Newton steps on P(rho) - target with the analytic
+// dP/drho, kept inside a shrinking bracket, converge from the ideal-gas estimate; a target
+// above the branch's top pressure gives the branch end.
+double inlet_density(const lbm_params_t &p, double Tc, double branch_end, long long t) {
+  const double T = Tc * p.T_inlet;
+  const double p0 = host_pressure(p, Tc, p.rho_out, T);
   const double s = p.u_period == 0.0 ? 1.0 : std::sin(2.0 * kPi * (double)t / p.u_period);
   const double target = p0 * (1.0 + p.p_amp_frac * s);
-  double lo = 0.0, hi = h->rho_branch_end;
-  for (int it = 0; it < 200; it++) {
-    const double mid = 0.5 * (lo + hi);
-    if (host_pressure(p, h->Tc, mid, T) < target) lo = mid; else hi = mid;
+  double lo = 0.0, hi = branch_end;
+  if (target >= host_pressure(p, Tc, hi, T)) return hi;
+  if (target <= 0.0) return 0.0;
+  const double k = 0.37464 + 1.54226 * p.eos_omega - 0.26992 * p.eos_omega * p.eos_omega;
+  const double r = 1.0 + k * (1.0 - std::sqrt(T / Tc));
+  const double aphi = p.eos_a * r * r;
+  double rho = std::min(target / (p.eos_R * T), 0.5 * hi);
+  for (int it = 0; it < 100; it++) {
+    const double f = host_pressure(p, Tc, rho, T) - target;
+    if (f == 0.0) break;
+    if (f < 0.0) lo = rho; else hi = rho;
+    const double br = p.eos_b * rho, D = 1.0 + 2.0 * br - br * br;
+    const double dP = p.eos_R * T / ((1.0 - br) * (1.0 - br)) -
+                      2.0 * aphi * rho * (1.0 + br) / (D * D);
+    double next = dP > 0.0 ? rho - f / dP : 0.5 * (lo + hi);
+    if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+    if (std::fabs(next - rho) <= 1e-15 * rho) {
+      rho = next;
+      break;
+    }
+    rho = next;
   }
-  return 0.5 * (lo + hi);
+  return rho;
 }
 
 }  // namespace
@@ -256,7 +336,9 @@ lbm::StepScalars lbm_host::scalars_at(const lbm_lattice *h, long long t) {
                                    : h->p.u_amp * std::sin(2.0 * kPi * (double)t / h->p.u_period);
   s.u_in = (float)u;
   s.gcos = (float)std::cos(h->p.g_omega * (double)t);
-  s.rho_in = h->p.x_bc == LBM_X_PRESSURE_INLET ? (float)inlet_density(h, t) : 0.0f;
+  s.rho_in = h->p.x_bc == LBM_X_PRESSURE_INLET
+                 ? (float)inlet_density(h->p, h->Tc, h->rho_branch_end, t)
+                 : 0.0f;
   return s;
 }
 
@@ -485,6 +567,16 @@ double lbm_critical_temperature(const lbm_params_t *p) {
   return p ? critical_temperature(*p) : 0.0;
 }
 
+int lbm_pressure_inlet_density(const lbm_params_t *p, long long t, double *rho) {
+  if (!p || !rho) return LBM_ERR_ARG;
+  if (!(p->eos_a > 0.0) || !(p->eos_b > 0.0) || !(p->eos_R > 0.0) || !(p->T_inlet > 0.0) ||
+      !(p->rho_out > 0.0) || !(std::fabs(p->p_amp_frac) < 1.0) || p->u_period < 0.0)
+    return LBM_ERR_ARG;
+  const double Tc = critical_temperature(*p);
+  *rho = inlet_density(*p, Tc, vapour_branch_end(*p, Tc, Tc * p->T_inlet), t);
+  return LBM_OK;
+}
+
 const char *lbm_strerror(int code) {
   switch (code) {
     case LBM_OK: return "ok";
@@ -519,18 +611,28 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
   if (p->x_bc == LBM_X_PRESSURE_INLET)
     h->rho_branch_end = vapour_branch_end(*p, h->Tc, h->Tc * p->T_inlet);
   h->kernel = LBM_KERNEL_SPLIT;
-  if (p->kernel == LBM_KERNEL_FUSED || p->kernel == LBM_KERNEL_AUTO) {
-    if (lbm::fused_supported(h->dp)) h->fused = lbm::fused_tiling(h->dp, p->storage, h->device);
+  if (p->kernel != LBM_KERNEL_SPLIT) {
+    // lattice columns per thread of the fused kernel: as asked, else the library's
+    // default, which LBM_FUSED_CPT=1|2 overrides (tuning experiments)
+    int cpt = default_cpt(nx, ny);
+    if (const char *env = std::getenv("LBM_FUSED_CPT")) {
+      const int v = std::atoi(env);
+      if (v == 1 || v == 2) cpt = v;
+    }
+    if (p->kernel == LBM_KERNEL_FUSED_1COL) cpt = 1;
+    if (p->kernel == LBM_KERNEL_FUSED_2COL) cpt = 2;
+    if (lbm::fused_supported(h->dp))
+      h->fused = lbm::fused_tiling(h->dp, p->storage, h->device, cpt);
     // LBM_FUSED_TILE="W,H" overrides the tiling (tuning experiments)
     if (const char *env = std::getenv("LBM_FUSED_TILE")) {
       int W = 0, H = 0;
-      if (std::sscanf(env, "%d,%d", &W, &H) == 2 && W >= 1 && W <= lbm::fused_max_width() &&
+      if (std::sscanf(env, "%d,%d", &W, &H) == 2 && W >= 1 && W <= lbm::fused_max_width(cpt) &&
           H >= 1 && (ny + H - 1) / H <= 65535 && lbm::fused_supported(h->dp))
-        h->fused = lbm::FusedTiling{W, H};
+        h->fused = lbm::FusedTiling{W, H, cpt};
     }
     if (h->fused.W > 0) {
       h->kernel = LBM_KERNEL_FUSED;
-    } else if (p->kernel == LBM_KERNEL_FUSED) {
+    } else if (p->kernel != LBM_KERNEL_AUTO) {
       delete h;
       return LBM_ERR_ARG;
     }
@@ -748,6 +850,7 @@ int lbm_info(lbm_h h, lbm_info_t *info) {
   const bool fused = h->kernel == LBM_KERNEL_FUSED;
   info->tile_cols = fused ? h->fused.W : 0;
   info->tile_rows = fused ? h->fused.H : 0;
+  info->cols_per_thread = fused ? h->fused.cpt : 0;
   return LBM_OK;
 }
 

@@ -37,7 +37,7 @@ namespace {
 using lbm_host::cuda_fail;
 
 int tiles_of(const lbm_lattice *h, int rows) {
-  const int W = lbm::fused_max_width();
+  const int W = lbm::fused_max_width(1);
   const int H = std::min(rows, h->ny);
   return ((h->nx + W - 1) / W) * ((h->ny + H - 1) / H);
 }
@@ -64,7 +64,7 @@ void layout(lbm_batch *b) {
 // returns the makespan in row steps and the number of tiles.
 double schedule(const lbm_batch *b, const std::vector<const lbm_lattice *> &order, int H,
                 long long &ntiles) {
-  const int W = lbm::fused_max_width();
+  const int W = lbm::fused_max_width(1);
   std::priority_queue<double, std::vector<double>, std::greater<double>> slots;
   for (int k = 0; k < b->grid; k++) slots.push(0.0);
   double makespan = 0.0;
@@ -134,7 +134,7 @@ int default_rows(const lbm_batch *b) {
 // Channel tables for the lattices' current buffers: table 0 for steps at even
 // offsets from now, table 1 for odd offsets.
 int upload_tables(lbm_batch *b, cudaStream_t s) {
-  const int W = lbm::fused_max_width();
+  const int W = lbm::fused_max_width(1);
   int begin = 0;
   for (int par = 0; par < 2; par++) b->h_ch[par].resize(b->lat.size());
   for (size_t i = 0; i < b->lat.size(); i++) {

@@ -38,10 +38,15 @@ __host__ __device__ constexpr float inv_wlat(int i) {
 //  F32 : stores g_i.
 //  BF16, F16 : store h_i = g_i / w_i = f_i / w_i - rho_ref, so that all nine
 //              directions share one range (16-bit, round to nearest).
+//  store2 writes the values of two adjacent columns (p 2-element aligned) with one
+//  store, rounding each exactly as pack does.
 struct StoreF32 {
   using T = float;
   static __device__ __forceinline__ float load(const T *p, int) { return __ldg(p); }
   static __device__ __forceinline__ T pack(float g, int) { return g; }
+  static __device__ __forceinline__ void store2(T *p, float a, float b, int) {
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+  }
 };
 struct StoreBF16 {
   using T = __nv_bfloat16;
@@ -51,6 +56,9 @@ struct StoreBF16 {
   static __device__ __forceinline__ T pack(float g, int i) {
     return __float2bfloat16_rn(g * inv_wlat(i));
   }
+  static __device__ __forceinline__ void store2(T *p, float a, float b, int i) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a * inv_wlat(i), b * inv_wlat(i));
+  }
 };
 struct StoreF16 {
   using T = __half;
@@ -58,6 +66,9 @@ struct StoreF16 {
     return wlat(i) * __half2float(__ldg(p));
   }
   static __device__ __forceinline__ T pack(float g, int i) { return __float2half_rn(g * inv_wlat(i)); }
+  static __device__ __forceinline__ void store2(T *p, float a, float b, int i) {
+    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a * inv_wlat(i), b * inv_wlat(i));
+  }
 };
 
 enum : unsigned {
@@ -318,12 +329,14 @@ __device__ __forceinline__ float sum9(const float g[9]) {
 // ---------------------------------------------------------------------------
 // Forces of Eqs. 9, 14 from the psi deviations of the 8 neighbours.
 // dpsin[i]: psi(x+e_i) - psi_r (ignored when solid); dpsi_c: own psi - psi_r.
-// With s = sum_solid w e (so sum_fluid w e = -s) and q = sum_fluid w psi e =
-// sum_fluid w dpsi e - psi_r s, the sum of Eq. 9 and Eq. 14 with the local psi
-// as psi_w is
-//   F = psi_c [ -G sum_fluid w dpsi e + ((G - Gw) psi_r - Gw dpsi_c) s ],
-// written so that no two psi-sized terms cancel in FP32.
-// Returns F and 9 |F_m|^2 / psi^2 = 9 G^2 |q|^2 (9 G^2 folded into c_theta).
+// With S = 3 sum_solid w e (exact: 3 w is 1 or 1/4) and the fluid part
+// Q = 3 sum_fluid w dpsi e = (d1 - d3) + (d5 - d7 + d8 - d6) / 4 (x; y alike, solid
+// neighbours counted as 0), the sum of Eq. 9 and Eq. 14 with the local psi as psi_w is
+//   F = psi_c [ -G Q + ((G - Gw) psi_r - Gw dpsi_c) S ] / 3
+//     = (-G psi_c / 3) Q + psi_c wc S / 3,
+// written so that no two psi-sized terms cancel in FP32 and so that, with no solid
+// neighbour (S = 0), F is the bulk product (-G psi_c / 3) Q bit for bit.
+// Returns F and 9 |F_m|^2 / psi^2 = G^2 |Q - psi_r S|^2 (G^2 folded into c_theta).
 // ---------------------------------------------------------------------------
 struct Force {
   float Fx, Fy, fm2;
@@ -332,26 +345,29 @@ struct Force {
 __device__ __forceinline__ Force interaction_force(const DevParams &p, float dpsi_c,
                                                    const float dpsin[9], unsigned solid_mask,
                                                    float psi_w_fixed) {
-  float qx = 0.f, qy = 0.f, sx = 0.f, sy = 0.f;
+  float d[9];
+  float Sx = 0.f, Sy = 0.f;
 #pragma unroll
   for (int i = 1; i < 9; i++) {
-    if (solid_mask & (1u << i)) {
-      sx += wpsi(i) * ex(i);
-      sy += wpsi(i) * ey(i);
-    } else {
-      qx += wpsi(i) * dpsin[i] * ex(i);
-      qy += wpsi(i) * dpsin[i] * ey(i);
-    }
+    const bool sol = (solid_mask >> i) & 1u;
+    d[i] = sol ? 0.0f : dpsin[i];
+    Sx += sol ? (i <= 4 ? 1.0f : 0.25f) * ex(i) : 0.0f;
+    Sy += sol ? (i <= 4 ? 1.0f : 0.25f) * ey(i) : 0.0f;
   }
+  const float d57 = d[5] - d[7], d86 = d[8] - d[6];
+  const float Qx = fmaf(0.25f, d57 + d86, d[1] - d[3]);
+  const float Qy = fmaf(0.25f, d57 - d86, d[2] - d[4]);
   const float psi_c = p.psi_r + dpsi_c;
   // wall coefficient: local psi_w by default, a fixed psi(rho_w) when rho_w > 0
   const float wc = psi_w_fixed > 0.0f ? p.G * p.psi_r - p.Gw * psi_w_fixed
                                       : p.wall_r - p.Gw * dpsi_c;
+  const float gpsi = fmaf(p.G3, dpsi_c, p.G3r);  // -G psi_c / 3
+  const float ws = psi_c * wc * (1.0f / 3.0f);
   Force F;
-  F.Fx = psi_c * fmaf(wc, sx, -p.G * qx);
-  F.Fy = psi_c * fmaf(wc, sy, -p.G * qy);
-  const float fx = fmaf(-p.psi_r, sx, qx), fy = fmaf(-p.psi_r, sy, qy);
-  F.fm2 = 9.0f * fmaf(fx, fx, fy * fy);
+  F.Fx = fmaf(ws, Sx, gpsi * Qx);
+  F.Fy = fmaf(ws, Sy, gpsi * Qy);
+  const float fx = fmaf(-p.psi_r, Sx, Qx), fy = fmaf(-p.psi_r, Sy, Qy);
+  F.fm2 = fmaf(fx, fx, fy * fy);
   return F;
 }
 

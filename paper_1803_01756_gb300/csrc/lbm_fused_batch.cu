@@ -55,8 +55,9 @@ __global__ void __launch_bounds__(FNT, LBM_FUSED_MIN_CTAS)
     const int Y0 = by * C.H;
     const typename ST::T *gs = static_cast<const typename ST::T *>(C.gs);
     typename ST::T *gout = static_cast<typename ST::T *>(C.gout);
-    fused_tile<YW, XO, TH, MP, ST, 1>(sp, sp, gs, gout, C.Tin, C.Tout, C.status, sc[s_ch], bx * C.W,
-                                   C.W, Y0, min(Y0 + C.H, sp.ny), S);
+    fused_tile<YW, XO, TH, MP, ST, 1, FNT, 1>(sp, sp, gs, gout, C.Tin, C.Tout, C.status,
+                                             sc[s_ch], bx * C.W, C.W, Y0,
+                                             min(Y0 + C.H, sp.ny), S);
     __syncthreads();
     if (threadIdx.x == 0) tile = (int)gridDim.x + atomicAdd(&counter[0], 1);
   }

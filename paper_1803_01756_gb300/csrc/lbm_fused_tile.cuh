@@ -1,10 +1,11 @@
 // Fused lattice update: the per-tile sweep shared by the single-lattice kernel
-// (lbm_fused.cu) and the batched kernel (lbm_fused_batch.cu).
+// (lbm_fused_step.cuh) and the batched kernel (lbm_fused_batch.cu).
 //
-// A CTA owns FW output columns and a chunk of H output rows.  Its FNT threads
-// each own one lattice column of [X0 - 5, X0 + FW + 5) and sweep the rows of the
-// chunk (plus 5 halo rows on each side) from bottom to top.  Per swept row the
-// update runs as six stages that trail each other by two rows:
+// A CTA of NT threads owns FW output columns and a chunk of H output rows.  Each
+// thread owns CPT adjacent lattice columns of [X0 - FH, X0 - FH + NT * CPT) (FH halo
+// columns on the left, at least 5 on the right) and sweeps the rows of the chunk
+// (plus 5 halo rows on each side) from bottom to top.  Per swept row the update runs
+// as six stages that trail each other by two rows:
 //   S0 row r     : pull-streaming with boundary rules (Eq. 12), density (Eq. 13),
 //                  pseudopotential deviation (Eqs. 10-11)            -> psi ring
 //   S1 row r-2   : forces (Eqs. 9, 14, 15), velocity (Eq. 13), MRT collision with
@@ -18,6 +19,14 @@
 // of the two newest rows) stay in registers.  Global traffic per cell-update is
 // the algorithmic minimum: the populations and T read once and written once,
 // plus halo re-reads that hit L2.
+//
+// With CPT = 2 a thread reads the stencil rows of its two columns and their two
+// outer neighbours with three shared-memory loads per row instead of six, shares
+// the per-row bookkeeping between the columns, gives the scheduler two independent
+// chains, and stores the populations and T of its column pair with 64-bit (FP32) or
+// 32-bit (16-bit storage) stores; FH = 6 keeps every pair's first column even.
+// Every column runs the same instructions whichever thread and slot hold it, so
+// a node gets the same bits for any tiling and either CPT.
 #pragma once
 
 #include "lbm_internal.h"
@@ -29,40 +38,112 @@ namespace {
 #ifndef LBM_FUSED_THREADS
 #define LBM_FUSED_THREADS 128
 #endif
-constexpr int FNT = LBM_FUSED_THREADS;  // threads per CTA, one lattice column each
+constexpr int FNT = LBM_FUSED_THREADS;  // threads per CTA of the CPT = 1 kernel
 #ifndef LBM_FUSED_MIN_CTAS
 #define LBM_FUSED_MIN_CTAS (512 / LBM_FUSED_THREADS)
 #endif
-constexpr int FHALO = 5;             // psi is needed 5 nodes beyond the outputs
-constexpr int FW = FNT - 2 * FHALO;  // output columns per CTA
 
-struct FusedSmem {
-  float4 pad_lo;        // neighbour reads of thread 0 below the first ring
-  float psi[4][FNT];    // psi - psi_r, rows j-3 .. j
-  float2 u[4][FNT];     // velocity, rows j-5 .. j-2
-  float4 cf[4][FNT];    // energy coefficients of rho (cl, E1/(3 div u), E2/(3 div u), -), same rows
-  float T[8][FNT];      // T - T_ref, rows j-5 .. j
-  float T2[4][FNT], T3[4][FNT], T4[4][FNT];  // RK stage fields
+// left halo columns of a CTA: psi is needed 5 nodes beyond the outputs; with two columns
+// per thread one more keeps the pairs aligned
+__host__ __device__ constexpr int fused_halo(int cpt) { return cpt == 1 ? 5 : 6; }
+// output columns of a CTA of nt threads with cpt columns each
+__host__ __device__ constexpr int fused_width(int nt, int cpt) {
+  return nt * cpt - fused_halo(cpt) - 5 - (cpt == 1 ? 0 : 1);
+}
+constexpr int FW = fused_width(FNT, 1);  // output columns of the CPT = 1 CTA
+
+template <int NC>
+struct FusedSmemT {
+  float4 pad_lo;         // neighbour reads of the first column below the first ring
+  float psi[4][NC];      // psi - psi_r, rows j-3 .. j
+  float2 u[4][NC];       // velocity, rows j-5 .. j-2
+  float4 cf[4][NC];      // energy coefficients of rho (cl, E1/(3 div u), E2/(3 div u), -), same rows
+  float T[8][NC];        // T - T_ref, rows j-5 .. j
+  float T2[4][NC], T3[4][NC], T4[4][NC];  // RK stage fields
   // own-column values of rows j-10 .. j-4: (ux/3, uy/3, cl, E1), (E2, Tb) and the RK4 sum
-  float4 o1[8][FNT];
-  float2 o2[8][FNT];
-  float oacc[8][FNT];
-  float4 pad_hi;        // neighbour reads of the last thread above the last ring
+  float4 o1[8][NC];
+  float2 o2[8][NC];
+  float oacc[8][NC];
+  float4 pad_hi;         // neighbour reads of the last column above the last ring
 };
+using FusedSmem = FusedSmemT<FNT>;
 
 __device__ __forceinline__ int modi(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
 }
 
-// Shared-memory ring access by a byte offset `off` of a float element (slot * FNT * 4 +
+// Shared-memory ring access by a byte offset `off` of a float element (slot * NC * 4 +
 // column * 4; +-4 for the neighbouring columns); rings of float2 and float4 elements
-// scale it by their element size, so one offset register serves every ring.
+// scale it by their element size, so one offset register serves every ring.  PF1 and PF2
+// address the pair of a thread's two columns in a float and a float2 ring.
 #define F1(ring, off) (*reinterpret_cast<float *>(reinterpret_cast<char *>(ring) + (off)))
 #define F2(ring, off) (*reinterpret_cast<float2 *>(reinterpret_cast<char *>(ring) + 2 * (off)))
 #define F4(ring, off) (*reinterpret_cast<float4 *>(reinterpret_cast<char *>(ring) + 4 * (off)))
+#define PF1(ring, off) (*reinterpret_cast<float2 *>(reinterpret_cast<char *>(ring) + (off)))
+#define PF2(ring, off) (*reinterpret_cast<float4 *>(reinterpret_cast<char *>(ring) + 2 * (off)))
 
-// K(T) of Eq. 16 at one node from a 3-row ring window of the stage field, with
+// One row of a float ring at the thread's CPT columns and one neighbour on each side:
+// v[0] = first column - 1, v[1 .. CPT] the own columns, v[CPT + 1] = last column + 1.
+template <int CPT>
+__device__ __forceinline__ void ring_row(float *ring, int off, float (&v)[CPT + 2]) {
+  v[0] = F1(ring, off - 4);
+  if constexpr (CPT == 1) {
+    v[1] = F1(ring, off);
+  } else {
+    const float2 a = PF1(ring, off);
+    v[1] = a.x;
+    v[2] = a.y;
+  }
+  v[CPT + 1] = F1(ring, off + 4 * CPT);
+}
+
+// the same for a float2 ring
+template <int CPT>
+__device__ __forceinline__ void ring_row2(float2 *ring, int off, float2 (&v)[CPT + 2]) {
+  v[0] = F2(ring, off - 4);
+  if constexpr (CPT == 1) {
+    v[1] = F2(ring, off);
+  } else {
+    const float4 a = PF2(ring, off);
+    v[1] = make_float2(a.x, a.y);
+    v[2] = make_float2(a.z, a.w);
+  }
+  v[CPT + 1] = F2(ring, off + 4 * CPT);
+}
+
+// Store the thread's column values into a float ring: one vector store when every column
+// writes, else one predicated store per column.
+template <int CPT>
+__device__ __forceinline__ void ring_put(float *ring, int off, const float (&v)[CPT], bool all,
+                                         const bool (&w)[CPT]) {
+  if constexpr (CPT == 2) {
+    if (all) {
+      PF1(ring, off) = make_float2(v[0], v[1]);
+      return;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CPT; k++)
+    if (w[k]) F1(ring, off + 4 * k) = v[k];
+}
+
+template <int CPT>
+__device__ __forceinline__ void ring_put2(float2 *ring, int off, const float2 (&v)[CPT], bool all,
+                                          const bool (&w)[CPT]) {
+  if constexpr (CPT == 2) {
+    if (all) {
+      PF2(ring, off) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+      return;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CPT; k++)
+    if (w[k]) F2(ring, off + 4 * k) = v[k];
+}
+
+// K(T) of Eq. 16 at column k of a 3-row window of the stage field (rows m = q - 1,
+// z = q, p = q + 1; index k + 1 is the node), with
 //   grad T = 3 sum w_i T(x+e_i) e_i = g / 3,    g_x = (T1 - T3) + (T5 - T7 + T8 - T6) / 4,
 //   lap T = 6 sum w_i (T(x+e_i) - T(x)) = 2 L / 3,
 //                                         L = (T1 + T2 + T3 + T4) + (T5 + T6 + T7 + T8) / 4 - 5T,
@@ -70,12 +151,14 @@ __device__ __forceinline__ int modi(int v, int n) {
 // and, with x = T/Tc = s^2, the last term equal to E1 x + E2 s (E1 = e1 Tc - e2 kappa,
 // E2 = e2 (1 + kappa)).  The caller passes us = u/3, cl = (2/3) lambda/(rho Cv), E1, E2:
 //   K = -us.g + cl L - E1 x - E2 s.
-__device__ __forceinline__ float rk_rate(const DevParams &p, float *__restrict__ R, int im,
-                                         int i0, int ip, float uxs, float uys, float cl, float E1,
+template <int CPT>
+__device__ __forceinline__ float rk_rate(const DevParams &p, const float (&m)[CPT + 2],
+                                         const float (&z)[CPT + 2], const float (&pp)[CPT + 2],
+                                         int k, float uxs, float uys, float cl, float E1,
                                          float E2) {
-  const float c = F1(R, i0);
-  const float v1 = F1(R, i0 + 4), v3 = F1(R, i0 - 4), v2 = F1(R, ip), v4 = F1(R, im);
-  const float v5 = F1(R, ip + 4), v6 = F1(R, ip - 4), v7 = F1(R, im - 4), v8 = F1(R, im + 4);
+  const float c = z[k + 1];
+  const float v1 = z[k + 2], v3 = z[k], v2 = pp[k + 1], v4 = m[k + 1];
+  const float v5 = pp[k + 2], v6 = pp[k], v7 = m[k], v8 = m[k + 2];
   const float d57 = v5 - v7, d86 = v8 - v6;
   const float gx = fmaf(0.25f, d57 + d86, v1 - v3);
   const float gy = fmaf(0.25f, d57 - d86, v2 - v4);
@@ -85,76 +168,116 @@ __device__ __forceinline__ float rk_rate(const DevParams &p, float *__restrict__
   return fmaf(-E2, s, fmaf(-E1, x, fmaf(cl, lap, -fmaf(uxs, gx, uys * gy))));
 }
 
+// Store the populations of the thread's output columns of one row: a vector store of the
+// column pair when both are outputs (the first column is even, so the pair is aligned).
+template <class ST, int CPT>
+__device__ __forceinline__ void store_pops(typename ST::T *__restrict__ dst, int plane,
+                                           const float (&gn)[CPT][9], const bool (&out)[CPT]) {
+  if constexpr (CPT == 2) {
+    if (out[0] && out[1]) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) ST::store2(dst + i * plane, gn[0][i], gn[1][i], i);
+      return;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CPT; k++)
+    if (out[k]) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) dst[i * plane + k] = ST::pack(gn[k][i], i);
+    }
+}
+
 // One tile of the fused update: output columns [X0, X0 + W) and rows [Y0, ye) of
 // one lattice.  p supplies the bulk physics constants, pg the lattice's geometry and
 // boundary data (sizes, walls, inlet/outlet, gravity).  Both kernels pass the same
 // parameter set for the two; the split keeps the per-lattice fields apart from the
 // constants that the single-lattice kernel reads from its constant bank.  Boundary modes and physics switches are
 // compile-time parameters: YW walls in y, XO open ends in x, TH energy equation,
-// MP pseudopotential forces; ST the population storage.
-template <bool YW, bool XO, bool TH, bool MP, class ST, int U>
+// MP pseudopotential forces; ST the population storage; U row steps per loop
+// iteration; NT threads of CPT columns each.  With CPT = 2, X0 must be even.
+template <bool YW, bool XO, bool TH, bool MP, class ST, int U, int NT, int CPT>
 __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &pg,
                                            const typename ST::T *__restrict__ gs,
                                            typename ST::T *__restrict__ gout,
                                            const float *__restrict__ Tin,
                                            float *__restrict__ Tout, unsigned *status,
                                            const StepScalars &sc, int X0, int W, int Y0, int ye,
-                                           FusedSmem &S) {
+                                           FusedSmemT<NT * CPT> &S) {
+  constexpr int NC = NT * CPT;
+  constexpr int FH = fused_halo(CPT);
   const int t = threadIdx.x;
-  const int c = X0 - FHALO + t;  // lattice column of this thread
-
-  // column kind: domain (wrapped when periodic) or a ghost beyond an open end
-  bool col_in = false, col_out = false;
-  int cx;
-  if (!XO) {
-    cx = modi(c, pg.nx);
-  } else {
-    col_in = c < 0;
-    col_out = c >= pg.nx;
-    cx = min(max(c, 0), pg.nx - 1);
-  }
+  const int c0 = X0 - FH + CPT * t;  // lattice column of this thread's first column
   const int xe = min(X0 + W, pg.nx);
-  const int dxo = c < X0 ? X0 - c : (c >= xe ? c - xe + 1 : 0);  // columns outside the outputs
+
+  // Per column: kind (domain, wrapped when periodic, or a ghost beyond an open end).
   // Ghost columns beyond an open end hold copies that the thread of the adjacent
-  // boundary column writes into their ring slots (same thread, no race): the outlet
-  // ghost copies column nx-1 (psi, T, u and the RK4 stage fields), the inlet ghost
-  // copies psi of column 0 (zero gradient) and holds T_inlet, and with a pressure inlet
-  // also copies the velocity of column 0.  Only the ghost column next to the domain is
-  // read by a needed stencil, so the other ghost threads do no work in S0.
-  const bool ghost = col_in || col_out;
-  const bool mirror = XO && c == pg.nx - 1 && t + 1 < FNT;
-  const bool mirror_in0 = XO && c == 0 && t >= 1;
-  const bool mirror_in = mirror_in0 && pg.p_inlet;
-  // the CTA holds a column of an open end (uniform over the CTA): only such CTAs have
-  // Zou-He unknowns to fix
-  const bool xb = XO && (c - t <= 0 || c - t + FNT - 1 >= pg.nx - 1);
+  // boundary column writes into their ring slots (no race: a ghost never writes its own
+  // slot): the outlet ghost copies column nx-1 (psi, T, u and the RK4 stage fields), the
+  // inlet ghost copies psi of column 0 (zero gradient) and holds T_inlet, and with a
+  // pressure inlet also copies the velocity of column 0.  Only the ghost column next to
+  // the domain is read by a needed stencil, so the other ghosts' values do not matter.
   // Energy-equation ghosts of the walls (Section 3.2): isothermal columns hold the wall
   // temperature of their wall; on adiabatic columns every stage field's ghost copies the
   // fluid node across the wall: at the top the ghost row takes the value of row ny - 1
   // written one row step earlier, at the bottom row 0 writes its value into the slot of
-  // row -1 (not read by any stage before then).  Adiabatic columns come with periodic x.
-  const float twall = wall_T_dev(pg, cx), twall_top = wall_T_top_dev(pg, cx);
-  // (lbm_create accepts adiabatic columns only with periodic x: compile-time false for open x)
-  const bool adi_bot = YW && !XO && pg.adiabatic && wall_adiabatic(pg, cx, false);
-  const bool adi_top = YW && !XO && pg.adiabatic && wall_adiabatic(pg, cx, true);
-
+  // row -1 (not read by any stage before then).  Adiabatic columns come with periodic x
+  // (lbm_create accepts them only then: compile-time false for open x).
+  int cx[CPT];
+  bool col_in[CPT], col_out[CPT], ghost[CPT], outc[CPT], mirror[CPT], mirror_in0[CPT],
+      mirror_in[CPT], adi_bot[CPT], adi_top[CPT];
+  bool wS0[CPT], wU[CPT], wT[CPT];  // the column writes its own slot in S0, S1 (u), S2-S4
+  float twall[CPT], twall_top[CPT];
   // Pull offsets relative to the node's own index (Eq. 12, f_i(x) = f*_i(x - e_i)), used
   // on every row not next to a wall.  Next to a periodic seam the source column wraps;
   // at an open end the populations entering from outside (Zou-He unknowns) read any
   // in-bounds element of their plane and are replaced by pull_fix.
-  int poff[9];
-  unsigned unk_edge = 0u;
+  int poff[CPT][9];
+  unsigned unk_edge[CPT];
+  bool allS0 = true, allU = true, allT = true;
 #pragma unroll
-  for (int i = 0; i < 9; i++) {
-    poff[i] = i * (int)pg.plane - ey(i) * pg.pitch - ex(i);
+  for (int k = 0; k < CPT; k++) {
+    const int c = c0 + k, lc = CPT * t + k;
+    col_in[k] = false;
+    col_out[k] = false;
     if (!XO) {
-      if (cx == 0 && ex(i) == 1) poff[i] += pg.nx;
-      if (cx == pg.nx - 1 && ex(i) == -1) poff[i] -= pg.nx;
+      cx[k] = modi(c, pg.nx);
     } else {
-      if (cx == 0 && ex(i) == 1) unk_edge |= 1u << i;
-      if (cx == pg.nx - 1 && ex(i) == -1) unk_edge |= 1u << i;
+      col_in[k] = c < 0;
+      col_out[k] = c >= pg.nx;
+      cx[k] = min(max(c, 0), pg.nx - 1);
+    }
+    outc[k] = c >= X0 && c < xe;
+    ghost[k] = col_in[k] || col_out[k];
+    mirror[k] = XO && c == pg.nx - 1 && lc + 1 < NC;
+    mirror_in0[k] = XO && c == 0 && lc >= 1;
+    mirror_in[k] = mirror_in0[k] && pg.p_inlet;
+    twall[k] = wall_T_dev(pg, cx[k]);
+    twall_top[k] = wall_T_top_dev(pg, cx[k]);
+    adi_bot[k] = YW && !XO && pg.adiabatic && wall_adiabatic(pg, cx[k], false);
+    adi_top[k] = YW && !XO && pg.adiabatic && wall_adiabatic(pg, cx[k], true);
+    wS0[k] = !ghost[k];
+    wU[k] = !col_out[k] && !(col_in[k] && pg.p_inlet);
+    wT[k] = !col_out[k];
+    allS0 = allS0 && wS0[k];
+    allU = allU && wU[k];
+    allT = allT && wT[k];
+    unk_edge[k] = 0u;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+      poff[k][i] = i * (int)pg.plane - ey(i) * pg.pitch - ex(i);
+      if (!XO) {
+        if (cx[k] == 0 && ex(i) == 1) poff[k][i] += pg.nx;
+        if (cx[k] == pg.nx - 1 && ex(i) == -1) poff[k][i] -= pg.nx;
+      } else {
+        if (cx[k] == 0 && ex(i) == 1) unk_edge[k] |= 1u << i;
+        if (cx[k] == pg.nx - 1 && ex(i) == -1) unk_edge[k] |= 1u << i;
+      }
     }
   }
+  // the CTA holds a column of an open end (uniform over the CTA): only such CTAs have
+  // Zou-He unknowns to fix
+  const bool xb = XO && (X0 - FH <= 0 || X0 - FH + NC - 1 >= pg.nx - 1);
 
   unsigned st = 0;
   // running checks folded into status bits once at the end
@@ -163,41 +286,53 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
   float drho_min = 0.0f;    // density must stay positive
   float drho_max = 0.0f;    // b rho must stay below the pole of Eq. 11
   float dT_min = 0.0f;      // absolute temperature must stay positive
-  float fA[9], fB[9];
-  float drhoA = 0.0f, drhoB = 0.0f;  // density deviations of the two newest pulled rows
+  float fA[CPT][9], fB[CPT][9];
+  float drhoA[CPT], drhoB[CPT];  // density deviations of the two newest pulled rows
 #pragma unroll
-  for (int i = 0; i < 9; i++) {
-    fA[i] = 0.0f;
-    fB[i] = 0.0f;
+  for (int k = 0; k < CPT; k++) {
+    drhoA[k] = 0.0f;
+    drhoB[k] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+      fA[k][i] = 0.0f;
+      fB[k][i] = 0.0f;
+    }
   }
 
-  // float byte offset of ring row (j - k) at this thread's column, shared by every ring
-  // and stage (R4(k), R8(k) below): q4[d] = 4 (((j + d) & 3) FNT + t),
-  // q8[d] = 4 (((j + d) & 7) FNT + t), rotated by one position per row step
+  // float byte offset of ring row (j - k) at this thread's first column, shared by every
+  // ring and stage (R4(k), R8(k) below): q4[d] = 4 (((j + d) & 3) NC + CPT t),
+  // q8[d] = 4 (((j + d) & 7) NC + CPT t), rotated by one position per row step.  The rings
+  // of own-column values (cf, o1, o2, oacc) hold column k of thread t at k NT + t of the
+  // slot (column-major over the thread's columns, so each column's access is
+  // conflict-free): OWN(q, k) = q - 4 (CPT - 1) t + 4 k NT.
   int q4[4], q8[8];
 #pragma unroll
-  for (int d = 0; d < 4; d++) q4[d] = 4 * (d * FNT + t);
+  for (int d = 0; d < 4; d++) q4[d] = 4 * (d * NC + CPT * t);
 #pragma unroll
-  for (int d = 0; d < 8; d++) q8[d] = 4 * (d * FNT + t);
+  for (int d = 0; d < 8; d++) q8[d] = 4 * (d * NC + CPT * t);
+  const int tsh = 4 * (CPT - 1) * t;
+#define OWN(q, k) ((q) - tsh + 4 * (k) * NT)
 
   // Stage conditions depend on the row only (uniform over the CTA).  Within a stage every
-  // thread computes, including halo threads outside the cone their stage is needed in
-  // (stage k is needed for dxo <= 5 - k) and ghost columns beyond an open end: those
-  // values are neither stored to global memory nor read by a needed column, and the
-  // ring writes that a boundary column mirrors into a ghost slot are predicated off in
-  // the ghost thread.  The pads around the rings keep the outermost threads' neighbour
-  // reads in bounds.
+  // thread computes, including halo columns outside the cone their stage is needed in
+  // (stage k is needed within 5 - k columns of the outputs) and ghost columns beyond an
+  // open end: those values are neither stored to global memory nor read by a needed
+  // column, and the ring writes that a boundary column mirrors into a ghost slot are
+  // predicated off in the ghost's own write.  The pads around the rings keep the
+  // outermost threads' neighbour reads in bounds.
   // Row ranges as one unsigned compare each: stage k (S1..S5) runs for 3k <= j < HR + 10 + k,
   // S0 for j < HR + 10, where HR is the number of output rows.
   const int HR = ye - Y0;
   const unsigned uny = (unsigned)pg.ny;
-  const int J = HR + 3 * FHALO;
-  // U = 2: two row steps per iteration, so that the compiler renames the rotated registers
-  // within the pair (a step past J, when J is odd, runs no stage: every stage range ends
-  // by J).  Measured, this pays in the single-lattice kernel (72.8 against 76.3 us on
-  // 4096 x 512) and costs in the batched one (23.5 against 25.5 GLUPS on 96 channels).
+  const int J = HR + 15;
+  // U = 2: two row steps per loop iteration, so that the compiler renames the rotated
+  // registers within the pair (a step past J, when J is odd, runs no stage: every stage
+  // range ends by J).  Each stage stores its ring values as soon as it has them: deferring
+  // all of a row step's ring stores to its end (no stage reads a slot another stage
+  // writes in the same step) raised the issue rate of the one-column kernel from 2.55 to
+  // 2.74 per cycle but added 14 % instructions at its 128-register bound, a net loss.
   auto row_step = [&](const int j) {
-    const int r = Y0 - FHALO + j;
+    const int r = Y0 - 5 + j;
 #define R4(k) q4[(4 - ((k) & 3)) & 3]
 #define R8(k) q8[(8 - ((k) & 7)) & 7]
     float *const ring_psi = &S.psi[0][0];
@@ -212,28 +347,39 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
     float *const ring_acc = &S.oacc[0][0];
 
     // ---------------- S0 loads: row r ----------------
-    const bool s0_row = j < HR + 2 * FHALO;
+    const bool s0_row = j < HR + 10;
     const bool r_solid = YW && (unsigned)r >= uny;
     const int ry = YW ? r : modi(r, pg.ny);
-    float fc[9];
-    unsigned unk = 0u;
-    float Tc = 0.0f, drhoC = 0.0f;
-    if (s0_row && !r_solid) {
-      // ghost threads load their clamped column (in bounds) and never use it
-      const int own = ry * pg.pitch + cx;
-      if ((unsigned)(ry - 1) < (unsigned)(pg.ny - 2)) {  // 0 < ry < ny - 1
-        const typename ST::T *src = gs + own;
+    float fc[CPT][9];
+    unsigned unk[CPT];
+    float Tc[CPT], drhoC[CPT];
 #pragma unroll
-        for (int i = 0; i < 9; i++) fc[i] = ST::load(src + poff[i], i);
-        unk = ghost ? 0u : unk_edge;
-      } else {
-        pull_load<ST>(pg, gs, cx, ry, fc, unk);
-        if (ghost) unk = 0u;
+    for (int k = 0; k < CPT; k++) {
+      unk[k] = 0u;
+      Tc[k] = 0.0f;
+      drhoC[k] = 0.0f;
+    }
+    if (s0_row && !r_solid) {
+#pragma unroll
+      for (int k = 0; k < CPT; k++) {
+        // ghost columns load their clamped column (in bounds) and never use it
+        const int own = ry * pg.pitch + cx[k];
+        if ((unsigned)(ry - 1) < (unsigned)(pg.ny - 2)) {  // 0 < ry < ny - 1
+          const typename ST::T *src = gs + own;
+#pragma unroll
+          for (int i = 0; i < 9; i++) fc[k][i] = ST::load(src + poff[k][i], i);
+          unk[k] = ghost[k] ? 0u : unk_edge[k];
+        } else {
+          pull_load<ST>(pg, gs, cx[k], ry, fc[k], unk[k]);
+          if (ghost[k]) unk[k] = 0u;
+        }
+        Tc[k] = __ldg(Tin + own);
       }
-      Tc = __ldg(Tin + own);
     } else {
 #pragma unroll
-      for (int i = 0; i < 9; i++) fc[i] = 0.0f;
+      for (int k = 0; k < CPT; k++)
+#pragma unroll
+        for (int i = 0; i < 9; i++) fc[k][i] = 0.0f;
     }
 
     // ---------------- S1: row r-2 (forces, velocity, collision) ----------------
@@ -243,83 +389,114 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
         const int sl = R4(2);
         const bool solid = YW && (unsigned)q >= uny;
         if (solid) {
-          if (TH) F2(ring_u, sl) = make_float2(0.0f, 0.0f);
+          if (TH) {
+            float2 z2[CPT];
+            bool yes[CPT];
+#pragma unroll
+            for (int k = 0; k < CPT; k++) {
+              z2[k] = make_float2(0.0f, 0.0f);
+              yes[k] = true;
+            }
+            ring_put2<CPT>(ring_u, sl, z2, true, yes);
+          }
         } else {
           const int qy = YW ? q : modi(q, pg.ny);
-          const float drho = drhoB;
-          const float rho = p.rho_ref + drho;
-          Force F{0.0f, 0.0f, 0.0f};
+          Force F[CPT];
+#pragma unroll
+          for (int k = 0; k < CPT; k++) F[k] = Force{0.0f, 0.0f, 0.0f};
           if (MP) {
-            const int pm = R4(3), p0 = R4(2), pp = R4(1);
+            float wm[CPT + 2], w0[CPT + 2], wp[CPT + 2];
+            ring_row<CPT>(ring_psi, R4(3), wm);
+            ring_row<CPT>(ring_psi, R4(2), w0);
+            ring_row<CPT>(ring_psi, R4(1), wp);
             const bool sdn = YW && q == 0;  // q is a fluid row here
             const bool sup = YW && q == pg.ny - 1;
-            float dn[9];
-            dn[0] = 0.0f;
-            dn[1] = F1(ring_psi, p0 + 4);
-            dn[2] = F1(ring_psi, pp);
-            dn[3] = F1(ring_psi, p0 - 4);
-            dn[4] = F1(ring_psi, pm);
-            dn[5] = F1(ring_psi, pp + 4);
-            dn[6] = F1(ring_psi, pp - 4);
-            dn[7] = F1(ring_psi, pm - 4);
-            dn[8] = F1(ring_psi, pm + 4);
-            const float dpc = F1(ring_psi, p0);
-            if (!sdn && !sup) {
-              // no wall neighbour: F = -G psi sum w dpsi e  (Eq. 9; sum w e = 0), with
-              // Q = 3 sum w dpsi e and fm2 = |Q|^2 = 9 |q|^2
-              const float d57 = dn[5] - dn[7], d86 = dn[8] - dn[6];
-              const float Qx = fmaf(0.25f, d57 + d86, dn[1] - dn[3]);
-              const float Qy = fmaf(0.25f, d57 - d86, dn[2] - dn[4]);
-              const float gpsi = fmaf(p.G3, dpc, p.G3r);  // -G psi / 3
-              F.Fx = gpsi * Qx;
-              F.Fy = gpsi * Qy;
-              F.fm2 = fmaf(Qx, Qx, Qy * Qy);
-            } else {
-              unsigned solid_mask = 0u;
-              if (sup) solid_mask |= (1u << 2) | (1u << 5) | (1u << 6);
-              if (sdn) solid_mask |= (1u << 4) | (1u << 7) | (1u << 8);
-              float psiw = 0.0f;
-              if (pg.rho_w > 0.0f) {
-                unsigned st_unused = 0;
-                psiw = pseudopotential(pg, pg.rho_w, p.T_ref + F1(ring_T, R8(2)), st_unused);
-              }
-              F = interaction_force(pg, dpc, dn, solid_mask, psiw);
-            }
-          }
-          if (pg.has_g) {
-            const float rho_v = pg.drho_ref_g + drho;  // rho - rho_v of Eq. 15
-            F.Fx += rho_v * pg.gx * sc.gcos;
-            F.Fy += rho_v * pg.gy * sc.gcos;
-          }
-          float ux, uy;
-          const float inv_rho = __fdividef(1.0f, rho);
-          if ((unsigned)(q - Y0) < (unsigned)HR) {
-            float gn[9], rr;
-            collide(p, fB, drho, F.Fx, F.Fy, F.fm2, gn, rr, ux, uy);
-            if (dxo == 0) {
-              typename ST::T *dst = gout + (qy * pg.pitch + c);
 #pragma unroll
-              for (int i = 0; i < 9; i++) dst[i * (int)pg.plane] = ST::pack(gn[i], i);
-              chk += ux + uy;  // rho enters at S0
+            for (int k = 0; k < CPT; k++) {
+              float dn[9];
+              dn[0] = 0.0f;
+              dn[1] = w0[k + 2];
+              dn[2] = wp[k + 1];
+              dn[3] = w0[k];
+              dn[4] = wm[k + 1];
+              dn[5] = wp[k + 2];
+              dn[6] = wp[k];
+              dn[7] = wm[k];
+              dn[8] = wm[k + 2];
+              const float dpc = w0[k + 1];
+              if (!sdn && !sup) {
+                // no wall neighbour: F = -G psi sum w dpsi e  (Eq. 9; sum w e = 0), with
+                // Q = 3 sum w dpsi e and fm2 = |Q|^2 = 9 |q|^2
+                const float d57 = dn[5] - dn[7], d86 = dn[8] - dn[6];
+                const float Qx = fmaf(0.25f, d57 + d86, dn[1] - dn[3]);
+                const float Qy = fmaf(0.25f, d57 - d86, dn[2] - dn[4]);
+                const float gpsi = fmaf(p.G3, dpc, p.G3r);  // -G psi / 3
+                F[k].Fx = gpsi * Qx;
+                F[k].Fy = gpsi * Qy;
+                F[k].fm2 = fmaf(Qx, Qx, Qy * Qy);
+              } else {
+                unsigned solid_mask = 0u;
+                if (sup) solid_mask |= (1u << 2) | (1u << 5) | (1u << 6);
+                if (sdn) solid_mask |= (1u << 4) | (1u << 7) | (1u << 8);
+                float psiw = 0.0f;
+                if (pg.rho_w > 0.0f) {
+                  unsigned st_unused = 0;
+                  psiw = pseudopotential(pg, pg.rho_w, p.T_ref + F1(ring_T, R8(2) + 4 * k),
+                                         st_unused);
+                }
+                F[k] = interaction_force(pg, dpc, dn, solid_mask, psiw);
+              }
             }
+          }
+          float ux[CPT], uy[CPT], rho[CPT], inv_rho[CPT];
+#pragma unroll
+          for (int k = 0; k < CPT; k++) {
+            const float drho = drhoB[k];
+            rho[k] = p.rho_ref + drho;
+            if (pg.has_g) {
+              const float rho_v = pg.drho_ref_g + drho;  // rho - rho_v of Eq. 15
+              F[k].Fx += rho_v * pg.gx * sc.gcos;
+              F[k].Fy += rho_v * pg.gy * sc.gcos;
+            }
+            inv_rho[k] = __fdividef(1.0f, rho[k]);
+          }
+          if ((unsigned)(q - Y0) < (unsigned)HR) {
+            float gn[CPT][9];
+#pragma unroll
+            for (int k = 0; k < CPT; k++) {
+              float rr;
+              collide(p, fB[k], drhoB[k], F[k].Fx, F[k].Fy, F[k].fm2, gn[k], rr, ux[k], uy[k]);
+              if (outc[k]) chk += ux[k] + uy[k];  // rho enters at S0
+            }
+            store_pops<ST, CPT>(gout + (qy * pg.pitch + c0), (int)pg.plane, gn, outc);
           } else {
-            float jxe, jye;
-            momentum(fB, F.Fx, F.Fy, jxe, jye);
-            ux = jxe * inv_rho;
-            uy = jye * inv_rho;
+#pragma unroll
+            for (int k = 0; k < CPT; k++) {
+              float jxe, jye;
+              momentum(fB[k], F[k].Fx, F[k].Fy, jxe, jye);
+              ux[k] = jxe * inv_rho[k];
+              uy[k] = jye * inv_rho[k];
+            }
           }
           if (TH) {
             // the velocity inlet's ghost holds the inlet velocity; with a pressure inlet
             // column 0 mirrors its velocity there
-            const float2 uu = col_in ? make_float2(sc.u_in, 0.0f) : make_float2(ux, uy);
-            if (!col_out && !(col_in && pg.p_inlet)) F2(ring_u, sl) = uu;
-            if (mirror) F2(ring_u, sl + 4) = uu;
-            if (mirror_in) F2(ring_u, sl - 4) = uu;
-            // energy coefficients of the node (see rk_rate): cl, E1 / (3 div u), E2 / (3 div u)
-            const float br = p.eos_b * rho;
-            const float z = __fdividef(p.akap1_cv3 * rho, fmaf(br, 2.0f - br, 1.0f));
-            F4(ring_cf, sl) = make_float4(p.lam23_cv * inv_rho,
-                                      __fdividef(p.RTc_cv3, 1.0f - br) - p.kappa_r * z, z, 0.0f);
+            float2 uu[CPT];
+#pragma unroll
+            for (int k = 0; k < CPT; k++)
+              uu[k] = col_in[k] ? make_float2(sc.u_in, 0.0f) : make_float2(ux[k], uy[k]);
+            ring_put2<CPT>(ring_u, sl, uu, allU, wU);
+#pragma unroll
+            for (int k = 0; k < CPT; k++) {
+              if (mirror[k]) F2(ring_u, sl + 4 * k + 4) = uu[k];
+              if (mirror_in[k]) F2(ring_u, sl + 4 * k - 4) = uu[k];
+              // energy coefficients of the node (see rk_rate): cl, E1 / (3 div u), E2 / (3 div u)
+              const float br = p.eos_b * rho[k];
+              const float z = __fdividef(p.akap1_cv3 * rho[k], fmaf(br, 2.0f - br, 1.0f));
+              F4(ring_cf, OWN(sl, k)) =
+                  make_float4(p.lam23_cv * inv_rho[k],
+                              __fdividef(p.RTc_cv3, 1.0f - br) - p.kappa_r * z, z, 0.0f);
+            }
           }
         }
       }
@@ -333,90 +510,120 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
           const int sl = R4(4);
           const bool solid = YW && (unsigned)q >= uny;
           if (solid) {
-            F1(ring_T2, sl) = q < 0 ? twall : (adi_top ? F1(ring_T2, R4(5)) : twall_top);
+#pragma unroll
+            for (int k = 0; k < CPT; k++)
+              F1(ring_T2, sl + 4 * k) =
+                  q < 0 ? twall[k] : (adi_top[k] ? F1(ring_T2, R4(5) + 4 * k) : twall_top[k]);
           } else {
-            const int um = R4(5), u0 = R4(4), up = R4(3);
-            const float2 a1 = F2(ring_u, u0 + 4), a3 = F2(ring_u, u0 - 4);
-            const float2 a2 = F2(ring_u, up), a4 = F2(ring_u, um);
-            const float2 a5 = F2(ring_u, up + 4), a6 = F2(ring_u, up - 4);
-            const float2 a7 = F2(ring_u, um - 4), a8 = F2(ring_u, um + 4);
-            // 3 div u = 9 sum w_i u(x+e_i).e_i (the 1/3 is folded into the cf coefficients)
-            const float divu3 = ((a1.x - a3.x) + (a2.y - a4.y)) +
-                                0.25f * ((a5.x + a5.y) - (a6.x - a6.y) - (a7.x + a7.y) +
-                                         (a8.x - a8.y));
-            const float2 uo = F2(ring_u, u0);
-            const float4 cf = F4(ring_cf, u0);
-            const float E1 = cf.y * divu3, E2 = cf.z * divu3;
-            const float uxs = uo.x * (1.0f / 3.0f), uys = uo.y * (1.0f / 3.0f);
-            const int t0 = R8(4);
-            const float Tb = F1(ring_T, t0);
-            const float h1 = rk_rate(p, ring_T, R8(5), t0, R8(3), uxs, uys, cf.x, E1, E2);
-            const float v = col_in ? pg.T_inlet_dev : Tb + 0.5f * h1;
-            if (!col_out) F1(ring_T2, sl) = v;
-            if (mirror) F1(ring_T2, sl + 4) = v;
-            if (adi_bot && q == 0) F1(ring_T2, R4(5)) = v;
-            F4(ring_o1, t0) = make_float4(uxs, uys, cf.x, E1);
-            F2(ring_o2, t0) = make_float2(E2, Tb);
-            F1(ring_acc, t0) = h1;
+            float2 um[CPT + 2], u0[CPT + 2], up[CPT + 2];
+            ring_row2<CPT>(ring_u, R4(5), um);
+            ring_row2<CPT>(ring_u, R4(4), u0);
+            ring_row2<CPT>(ring_u, R4(3), up);
+            float tm[CPT + 2], t0[CPT + 2], tp[CPT + 2];
+            ring_row<CPT>(ring_T, R8(5), tm);
+            ring_row<CPT>(ring_T, R8(4), t0);
+            ring_row<CPT>(ring_T, R8(3), tp);
+            const int o = R8(4);
+            float v[CPT];
+#pragma unroll
+            for (int k = 0; k < CPT; k++) {
+              const float2 a1 = u0[k + 2], a3 = u0[k];
+              const float2 a2 = up[k + 1], a4 = um[k + 1];
+              const float2 a5 = up[k + 2], a6 = up[k];
+              const float2 a7 = um[k], a8 = um[k + 2];
+              // 3 div u = 9 sum w_i u(x+e_i).e_i (the 1/3 is folded into the cf coefficients)
+              const float divu3 = ((a1.x - a3.x) + (a2.y - a4.y)) +
+                                  0.25f * ((a5.x + a5.y) - (a6.x - a6.y) - (a7.x + a7.y) +
+                                           (a8.x - a8.y));
+              const float2 uo = u0[k + 1];
+              const float4 cf = F4(ring_cf, OWN(R4(4), k));
+              const float E1 = cf.y * divu3, E2 = cf.z * divu3;
+              const float uxs = uo.x * (1.0f / 3.0f), uys = uo.y * (1.0f / 3.0f);
+              const float Tb = t0[k + 1];
+              const float h1 = rk_rate<CPT>(p, tm, t0, tp, k, uxs, uys, cf.x, E1, E2);
+              v[k] = col_in[k] ? pg.T_inlet_dev : Tb + 0.5f * h1;
+              F4(ring_o1, OWN(o, k)) = make_float4(uxs, uys, cf.x, E1);
+              F2(ring_o2, OWN(o, k)) = make_float2(E2, Tb);
+              F1(ring_acc, OWN(o, k)) = h1;
+            }
+            ring_put<CPT>(ring_T2, sl, v, allT, wT);
+#pragma unroll
+            for (int k = 0; k < CPT; k++) {
+              if (mirror[k]) F1(ring_T2, sl + 4 * k + 4) = v[k];
+              if (adi_bot[k] && q == 0) F1(ring_T2, R4(5) + 4 * k) = v[k];
+            }
           }
         }
       }
-      // ---------------- S3: row r-6 (h2) ----------------
-      {
-        const int q = r - 6;
-        if ((unsigned)(j - 9) < (unsigned)(HR + 4)) {
-          const int sl = R4(6);
-          const bool solid = YW && (unsigned)q >= uny;
-          if (solid) {
-            F1(ring_T3, sl) = q < 0 ? twall : (adi_top ? F1(ring_T3, R4(7)) : twall_top);
-          } else {
-            const int o = R8(6);
-            const float4 w1 = F4(ring_o1, o);
-            const float2 w2 = F2(ring_o2, o);
-            const float h2 = rk_rate(p, ring_T2, R4(7), sl, R4(5), w1.x, w1.y, w1.z, w1.w, w2.x);
-            const float v = col_in ? pg.T_inlet_dev : w2.y + 0.5f * h2;
-            if (!col_out) F1(ring_T3, sl) = v;
-            if (mirror) F1(ring_T3, sl + 4) = v;
-            if (adi_bot && q == 0) F1(ring_T3, R4(7)) = v;
-            F1(ring_acc, o) += 2.0f * h2;
+      // ---------------- S3: row r-6 (h2) and S4: row r-8 (h3) ----------------
+      // T2 -> T3 with the half step, T3 -> T4 with the full step
+      auto mid_stage = [&](const int q, const bool active, const int sl, const int below,
+                           const int above, const int o, float *const src, float *const dst,
+                           const bool full) {
+        if (!active) return;
+        const bool solid = YW && (unsigned)q >= uny;
+        if (solid) {
+#pragma unroll
+          for (int k = 0; k < CPT; k++)
+            F1(dst, sl + 4 * k) =
+                q < 0 ? twall[k] : (adi_top[k] ? F1(dst, below + 4 * k) : twall_top[k]);
+        } else {
+          float sm[CPT + 2], s0[CPT + 2], sp[CPT + 2];
+          ring_row<CPT>(src, below, sm);
+          ring_row<CPT>(src, sl, s0);
+          ring_row<CPT>(src, above, sp);
+          float v[CPT];
+#pragma unroll
+          for (int k = 0; k < CPT; k++) {
+            const float4 w1 = F4(ring_o1, OWN(o, k));
+            const float2 w2 = F2(ring_o2, OWN(o, k));
+            const float h = rk_rate<CPT>(p, sm, s0, sp, k, w1.x, w1.y, w1.z, w1.w, w2.x);
+            v[k] = col_in[k] ? pg.T_inlet_dev : (full ? w2.y + h : w2.y + 0.5f * h);
+            F1(ring_acc, OWN(o, k)) += 2.0f * h;
+          }
+          ring_put<CPT>(dst, sl, v, allT, wT);
+#pragma unroll
+          for (int k = 0; k < CPT; k++) {
+            if (mirror[k]) F1(dst, sl + 4 * k + 4) = v[k];
+            if (adi_bot[k] && q == 0) F1(dst, below + 4 * k) = v[k];
           }
         }
-      }
-      // ---------------- S4: row r-8 (h3) ----------------
-      {
-        const int q = r - 8;
-        if ((unsigned)(j - 12) < (unsigned)(HR + 2)) {
-          const int sl = R4(8);
-          const bool solid = YW && (unsigned)q >= uny;
-          if (solid) {
-            F1(ring_T4, sl) = q < 0 ? twall : (adi_top ? F1(ring_T4, R4(9)) : twall_top);
-          } else {
-            const int o = R8(8);
-            const float4 w1 = F4(ring_o1, o);
-            const float2 w2 = F2(ring_o2, o);
-            const float h3 = rk_rate(p, ring_T3, R4(9), sl, R4(7), w1.x, w1.y, w1.z, w1.w, w2.x);
-            const float v = col_in ? pg.T_inlet_dev : w2.y + h3;
-            if (!col_out) F1(ring_T4, sl) = v;
-            if (mirror) F1(ring_T4, sl + 4) = v;
-            if (adi_bot && q == 0) F1(ring_T4, R4(9)) = v;
-            F1(ring_acc, o) += 2.0f * h3;
-          }
-        }
-      }
+      };
+      mid_stage(r - 6, (unsigned)(j - 9) < (unsigned)(HR + 4), R4(6), R4(7), R4(5), R8(6),
+                ring_T2, ring_T3, false);
+      mid_stage(r - 8, (unsigned)(j - 12) < (unsigned)(HR + 2), R4(8), R4(9), R4(7), R8(8),
+                ring_T3, ring_T4, true);
       // ---------------- S5: row r-10 (h4, new temperature) ----------------
       {
         const int q = r - 10;
         if ((unsigned)(j - 15) < (unsigned)HR) {
+          float sm[CPT + 2], s0[CPT + 2], sp[CPT + 2];
+          ring_row<CPT>(ring_T4, R4(11), sm);
+          ring_row<CPT>(ring_T4, R4(10), s0);
+          ring_row<CPT>(ring_T4, R4(9), sp);
           const int o = R8(10);
-          const float4 w1 = F4(ring_o1, o);
-          const float2 w2 = F2(ring_o2, o);
-          const float h4 = rk_rate(p, ring_T4, R4(11), R4(10), R4(9), w1.x, w1.y, w1.z, w1.w,
-                                   w2.x);
-          const float Tn = w2.y + (F1(ring_acc, o) + h4) * (1.0f / 6.0f);
-          if (dxo == 0) {
-            chk += Tn;
-            dT_min = fminf(dT_min, Tn);
-            Tout[q * pg.pitch + c] = Tn;
+          float Tn[CPT];
+#pragma unroll
+          for (int k = 0; k < CPT; k++) {
+            const float4 w1 = F4(ring_o1, OWN(o, k));
+            const float2 w2 = F2(ring_o2, OWN(o, k));
+            const float h4 = rk_rate<CPT>(p, sm, s0, sp, k, w1.x, w1.y, w1.z, w1.w, w2.x);
+            Tn[k] = w2.y + (F1(ring_acc, OWN(o, k)) + h4) * (1.0f / 6.0f);
+            if (outc[k]) {
+              chk += Tn[k];
+              dT_min = fminf(dT_min, Tn[k]);
+            }
+          }
+          float *dst = Tout + (q * pg.pitch + c0);
+          bool pair = false;
+          if constexpr (CPT == 2) {
+            pair = outc[0] && outc[1];
+            if (pair) *reinterpret_cast<float2 *>(dst) = make_float2(Tn[0], Tn[1]);
+          }
+          if (!pair) {
+#pragma unroll
+            for (int k = 0; k < CPT; k++)
+              if (outc[k]) dst[k] = Tn[k];
           }
         }
       }
@@ -426,42 +633,56 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
     if (s0_row) {
       const int sl = R4(0), sT = R8(0);
       if (r_solid) {
-        F1(ring_T, sT) = r < 0 ? twall : (adi_top ? F1(ring_T, R8(1)) : twall_top);
-        F1(ring_psi, sl) = 0.0f;
+#pragma unroll
+        for (int k = 0; k < CPT; k++) {
+          F1(ring_T, sT + 4 * k) =
+              r < 0 ? twall[k] : (adi_top[k] ? F1(ring_T, R8(1) + 4 * k) : twall_top[k]);
+          F1(ring_psi, sl + 4 * k) = 0.0f;
+        }
       } else {
-        if (xb) pull_fix(pg, cx, sc, fc, unk);
-        float dpsi = 0.0f;
-        const float drho = sum9(fc);
-        drhoC = drho;
-        unsigned st_psi = 0u;
-        if (MP) dpsi = pseudopotential_dev(p, drho, Tc, st_psi);
-        if (!ghost) {
-          st |= st_psi;  // a ghost's populations include unfixed placeholders
-          F1(ring_T, sT) = Tc;
-          F1(ring_psi, sl) = dpsi;
-          drho_min = fminf(drho_min, drho);
-          drho_max = fmaxf(drho_max, drho);
-          dT_min = fminf(dT_min, Tc);
-          chk += drho;
+        float dpsi[CPT];
+#pragma unroll
+        for (int k = 0; k < CPT; k++) {
+          if (xb) pull_fix(pg, cx[k], sc, fc[k], unk[k]);
+          dpsi[k] = 0.0f;
+          const float drho = sum9(fc[k]);
+          drhoC[k] = drho;
+          unsigned st_psi = 0u;
+          if (MP) dpsi[k] = pseudopotential_dev(p, drho, Tc[k], st_psi);
+          if (!ghost[k]) {
+            st |= st_psi;  // a ghost's populations include unfixed placeholders
+            drho_min = fminf(drho_min, drho);
+            drho_max = fmaxf(drho_max, drho);
+            dT_min = fminf(dT_min, Tc[k]);
+            chk += drho;
+          }
         }
-        if (mirror) {
-          F1(ring_T, sT + 4) = Tc;
-          F1(ring_psi, sl + 4) = dpsi;
+        ring_put<CPT>(ring_T, sT, Tc, allS0, wS0);
+        ring_put<CPT>(ring_psi, sl, dpsi, allS0, wS0);
+#pragma unroll
+        for (int k = 0; k < CPT; k++) {
+          if (mirror[k]) {
+            F1(ring_T, sT + 4 * k + 4) = Tc[k];
+            F1(ring_psi, sl + 4 * k + 4) = dpsi[k];
+          }
+          if (mirror_in0[k]) {
+            F1(ring_T, sT + 4 * k - 4) = pg.T_inlet_dev;
+            F1(ring_psi, sl + 4 * k - 4) = dpsi[k];
+          }
+          if (adi_bot[k] && r == 0) F1(ring_T, R8(1) + 4 * k) = Tc[k];
         }
-        if (mirror_in0) {
-          F1(ring_T, sT - 4) = pg.T_inlet_dev;
-          F1(ring_psi, sl - 4) = dpsi;
-        }
-        if (adi_bot && r == 0) F1(ring_T, R8(1)) = Tc;
       }
     }
 #pragma unroll
-    for (int i = 0; i < 9; i++) {
-      fB[i] = fA[i];
-      fA[i] = fc[i];
+    for (int k = 0; k < CPT; k++) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) {
+        fB[k][i] = fA[k][i];
+        fA[k][i] = fc[k][i];
+      }
+      drhoB[k] = drhoA[k];
+      drhoA[k] = drhoC[k];
     }
-    drhoB = drhoA;
-    drhoA = drhoC;
     {
       const int a = q4[0];
 #pragma unroll
@@ -495,6 +716,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
   if (!(p.eos_b * (p.rho_ref + drho_max) < 1.0f)) st |= ST_EOS_POLE;
   if (!(p.T_ref + dT_min > 0.0f)) st |= ST_T_NONPOS;
   set_status(status, st);
+#undef OWN
 }
 
 }  // namespace

@@ -28,7 +28,7 @@ struct lbm_lattice {
   double rho_branch_end = 0;  // vapour-branch end of the isotherm at T_inlet (pressure inlet)
   long long t = 0;
   int kernel = LBM_KERNEL_SPLIT;
-  lbm::FusedTiling fused{0, 0};  // CTA tiling of the fused kernel
+  lbm::FusedTiling fused{0, 0, 1};  // CTA tiling of the fused kernel
   int cur = 0;   // g[cur]: post-collision populations of the previous update
   int tcur = 0;  // T[tcur]: temperature deviation of time t
   void *g[2] = {nullptr, nullptr};  // populations, storage-typed elements

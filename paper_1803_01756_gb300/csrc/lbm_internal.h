@@ -36,16 +36,26 @@ struct BatchChannel {
 
 // fused path: one launch per update; sc points to the update's scalars in device memory
 struct FusedTiling {
-  int W;  // output columns per CTA (at most 118)
-  int H;  // output rows per CTA
+  int W;    // output columns per CTA (at most fused_max_width(cpt))
+  int H;    // output rows per CTA
+  int cpt;  // lattice columns per thread: 1 or 2
 };
 cudaError_t launch_fused(const DevParams &p, int storage, const void *gs, void *gout,
                          const float *Tin, float *Tout, unsigned *status, const StepScalars *sc,
                          FusedTiling tiling, cudaStream_t s);
 bool fused_supported(const DevParams &p);
-// tiling for one wave of resident CTAs on this device ({0, 0} on failure); also sets
-// the kernel's shared-memory attribute
-FusedTiling fused_tiling(const DevParams &p, int storage, int device);
+// tiling for one wave of resident CTAs on this device with cpt columns per thread
+// ({0, 0, cpt} on failure); also sets the kernel's shared-memory attribute
+FusedTiling fused_tiling(const DevParams &p, int storage, int device, int cpt);
+// output columns of one CTA of the fused kernel with cpt columns per thread
+int fused_max_width(int cpt);
+// the CPT = 2 kernel (lbm_fused_c2.cu): threads per CTA, occupancy, launch on a grid of
+// (strips, row chunks)
+int fused_c2_threads();
+cudaError_t fused_c2_prepare(const DevParams &p, int storage, int *occ);
+cudaError_t fused_c2_launch(const DevParams &p, int storage, const void *gs, void *gout,
+                            const float *Tin, float *Tout, unsigned *status, const StepScalars *sc,
+                            dim3 grid, cudaStream_t s);
 
 // batched fused path: a persistent grid of `grid` CTAs walks the tiles of nch
 // lattices (all with the modes of `mode` and storage `storage`); counter: two ints,
@@ -55,7 +65,6 @@ cudaError_t launch_fused_batch(const DevParams &mode, int storage, const BatchCh
                                cudaStream_t s);
 // resident CTAs of the batched kernel on this device (0 on failure)
 int fused_batch_grid(const DevParams &mode, int storage, int device);
-int fused_max_width();
 
 // set-up and reductions
 cudaError_t launch_init(const DevParams &p, int storage, const double *rho0, void *gout,

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm_gb300.so")
 LBM_OK = 0
 ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_UNSTABLE",
           -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_BUSY", -7: "LBM_ERR_STATE"}
-KERNEL_AUTO, KERNEL_SPLIT, KERNEL_FUSED = 0, 1, 2
+KERNEL_AUTO, KERNEL_SPLIT, KERNEL_FUSED, KERNEL_FUSED_1COL, KERNEL_FUSED_2COL = 0, 1, 2, 3, 4
 STORAGE_F32 = 0
 
 
@@ -57,7 +57,7 @@ class LbmInfo(ctypes.Structure):
                 ("t", ctypes.c_longlong), ("Tc", ctypes.c_double), ("T_ref", ctypes.c_double),
                 ("rho_ref", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
                 ("kernel", ctypes.c_int), ("tile_cols", ctypes.c_int),
-                ("tile_rows", ctypes.c_int)]
+                ("tile_rows", ctypes.c_int), ("cols_per_thread", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -70,6 +70,12 @@ class ServerStats(ctypes.Structure):
                 ("completed", ctypes.c_long), ("failed", ctypes.c_long),
                 ("rounds", ctypes.c_long), ("bytes_in_use", ctypes.c_size_t),
                 ("peak_bytes", ctypes.c_size_t)]
+
+
+class DropletStats(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int * 2), ("spacing", ctypes.c_double * 2),
+                ("condensed_mass", ctypes.c_double), ("liquid_nodes", ctypes.c_longlong),
+                ("detached", ctypes.c_int)]
 
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE = 0, 1, 2
@@ -96,6 +102,8 @@ SIGNATURES = {
     "lbm_destroy": ([_vp], None),
     "lbm_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "lbm_critical_temperature": ([ctypes.POINTER(LbmParams)], ctypes.c_double),
+    "lbm_pressure_inlet_density": ([ctypes.POINTER(LbmParams), ctypes.c_longlong, _dp],
+                                   ctypes.c_int),
     "lbm_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                           ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "lbm_batch_step": ([_vp, ctypes.c_long, _vp], ctypes.c_int),
@@ -114,6 +122,8 @@ SIGNATURES = {
     "lbm_wait": ([_vp, ctypes.c_long, ctypes.c_double, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lbm_server_stats": ([_vp, ctypes.POINTER(ServerStats)], ctypes.c_int),
     "lbm_server_destroy": ([_vp], None),
+    "lbm_droplet_stats": ([_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                           ctypes.c_int, ctypes.POINTER(DropletStats)], ctypes.c_int),
     "lbm_mass_heat_noalloc": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                ctypes.c_double, _vp, _vp], ctypes.c_int),
 }
@@ -179,6 +189,30 @@ def _dptr(a: np.ndarray | None):
     if a is None:
         return None
     return a.ctypes.data_as(_dp)
+
+
+def droplet_stats(rho: np.ndarray, threshold: float, rho_v: float,
+                  periodic_x: bool = False) -> dict:
+    """Droplet count and spacing per wall, condensed mass and liquid nodes of a host
+    density field [ny][nx] (lbm_droplet_stats; host-side call, no GPU needed)."""
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    ny, nx = r.shape
+    out = DropletStats()
+    _check(load_library().lbm_droplet_stats(_dptr(r), nx, ny, float(threshold), float(rho_v),
+                                            int(bool(periodic_x)), ctypes.byref(out)),
+           "lbm_droplet_stats")
+    return {"count": list(out.count), "spacing": list(out.spacing),
+            "condensed_mass": out.condensed_mass, "liquid_nodes": out.liquid_nodes,
+            "detached": out.detached}
+
+
+def pressure_inlet_density(params: dict, t: int) -> float:
+    """Density the pressure inlet imposes at time t (host-side call, no GPU needed)."""
+    out = ctypes.c_double()
+    p = make_params(params)
+    _check(load_library().lbm_pressure_inlet_density(ctypes.byref(p), int(t), ctypes.byref(out)),
+           "lbm_pressure_inlet_density")
+    return out.value
 
 
 class Lattice:

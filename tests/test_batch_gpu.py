@@ -66,7 +66,7 @@ def test_batch_equals_alone(graph, tile_rows):
         rho, ux, uy, T = lat.read_fields()
         rr, rux, ruy, rT = ref
         assert np.abs(rho - rr).max() <= 1e-5 * np.abs(rr).max()
-        assert np.hypot(ux - rux, uy - ruy).max() <= 1e-5 * max(np.hypot(rux, ruy).max(), 1e-2)
+        assert np.hypot(ux - rux, uy - ruy).max() <= 1e-5 * max(np.hypot(rux, ruy).max(), 1e-3)
         assert np.abs(T - rT).max() <= 1e-5 * np.abs(rT).max()
         assert lat.status() == 0
     b.close()
@@ -156,6 +156,6 @@ def test_batch_against_the_oracle(storage):
         o.step(150)
         rr, rux, ruy, rT = o.fields()
         assert np.abs(rho - rr).max() <= tol["rho"] * np.abs(rr).max()
-        assert np.hypot(ux - rux, uy - ruy).max() <= tol["u"] * max(np.hypot(rux, ruy).max(), 1e-2)
+        assert np.hypot(ux - rux, uy - ruy).max() <= tol["u"] * max(np.hypot(rux, ruy).max(), 1e-3)
         assert np.abs(T - rT).max() <= tol["T"] * np.abs(rT).max()
         lat.close()

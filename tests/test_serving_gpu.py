@@ -32,10 +32,10 @@ def job_set(n, seed):
     return jobs
 
 
-def alone(job):
+def alone(job, storage=0):
     from paper_1803_01756_gb300.lattice import Lattice
     nx, ny, p, steps, rho0 = job
-    lat = Lattice(nx, ny, p, kernel=2)
+    lat = Lattice(nx, ny, p, kernel=2, storage=storage)
     lat.write_fields(rho0)
     lat.step(steps)
     out = lat.read_fields()
@@ -43,21 +43,33 @@ def alone(job):
     return out
 
 
-def assert_same(got, ref):
+# A job in the mix runs in the batched kernel, alone in the single-lattice kernel; the
+# two compute the same update, so each job's fields must agree within the FP32 parity
+# bound in either storage (measured on GB300: bitwise equal in FP32, BF16 and FP16).
+SAME_BOUNDS = {0: {"rho": 1e-5, "u": 1e-5, "T": 1e-5},
+               1: {"rho": 1e-5, "u": 1e-5, "T": 1e-5}}
+
+
+def assert_same(got, ref, storage=0):
     rho, ux, uy, T = got
     rr, rux, ruy, rT = ref
-    assert np.abs(rho - rr).max() <= 1e-5 * np.abs(rr).max()
-    assert np.hypot(ux - rux, uy - ruy).max() <= 1e-5 * max(np.hypot(rux, ruy).max(), 1e-2)
-    assert np.abs(T - rT).max() <= 1e-5 * np.abs(rT).max()
+    b = SAME_BOUNDS[storage]
+    err = {"rho": np.abs(rho - rr).max() / np.abs(rr).max(),
+           "u": np.hypot(ux - rux, uy - ruy).max() / max(np.hypot(rux, ruy).max(), 1e-3),
+           "T": np.abs(T - rT).max() / np.abs(rT).max()}
+    assert all(err[k] <= b[k] for k in b), err
+    return err
 
 
-def test_jobs_in_the_mix_equal_jobs_alone():
+@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+def test_jobs_in_the_mix_equal_jobs_alone(storage):
+    """Both storages: FP32, and BF16, the storage the serving workload runs."""
     from paper_1803_01756_gb300.lattice import JOB_DONE, Server
     jobs = job_set(9, seed=70)
     srv = Server(hbm_budget=1 << 34, max_active=8, chunk_steps=24)
     ids = []
     for k, (nx, ny, p, steps, rho0) in enumerate(jobs):
-        ids.append(srv.submit(nx, ny, p, steps, rho0))
+        ids.append(srv.submit(nx, ny, p, steps, rho0, storage=storage))
         if k % 3 == 2:
             time.sleep(0.05)  # later jobs arrive while earlier ones run
     for jid in ids:
@@ -67,7 +79,7 @@ def test_jobs_in_the_mix_equal_jobs_alone():
     for jid, job in zip(ids, jobs):
         state, fields, latency = srv.poll(jid, fields=True)
         assert state == JOB_DONE and latency > 0
-        assert_same(fields, alone(job))
+        assert_same(fields, alone(job, storage), storage)
     srv.close()
 
 
