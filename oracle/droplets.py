@@ -16,6 +16,28 @@ from __future__ import annotations
 import numpy as np
 
 
+def contact_angle(rho: np.ndarray, rho_mid: float) -> float:
+    """Contact angle of a sessile cap on the bottom wall (wall at y = -1/2): 2 atan(2h / w)
+    from the cap height h on its centre column and the base width w along row 0, both with
+    linear interpolation of the rho_mid crossing (the reading of the droplet measure)."""
+    row = rho[0]
+    xs = np.where(row > rho_mid)[0]
+    if xs.size == 0:
+        return 180.0  # the drop has lifted off the wall
+    if xs.size == row.size:
+        return 0.0  # a film covers the wall
+    x0, x1 = xs.min(), xs.max()
+    left = x0 - (row[x0] - rho_mid) / (row[x0] - row[x0 - 1])
+    right = x1 + (row[x1] - rho_mid) / (row[x1] - row[x1 + 1])
+    w = right - left
+    c = int(round(0.5 * (x0 + x1)))
+    colv = rho[:, c]
+    ys = np.where(colv > rho_mid)[0]
+    y1 = ys.max()
+    h = y1 + (colv[y1] - rho_mid) / (colv[y1] - colv[y1 + 1]) + 0.5
+    return float(np.degrees(2 * np.arctan(2 * h / w)))
+
+
 def droplet_stats(rho: np.ndarray, threshold: float, rho_v: float,
                   periodic_x: bool = False) -> dict:
     from scipy import ndimage

@@ -57,6 +57,20 @@ RHO_L_086 = 6.498946
 # 0.86 Tc (tests/golden/theta_calibration.json, written from the oracle).
 THETA = 0.1112
 
+# Contact angle (degrees) of a sessile drop at 0.86 Tc against the wall strength G_w of
+# Eq. 14 (psi_w = local psi), from the oracle (tests/golden/contact_angle_table.json,
+# written by tests/golden/make_contact_angle_table.py; a test checks these literals
+# against that file).  Increasing in G_w; the drop lifts off above -1.07.
+CA_TABLE_GW = (-1.24, -1.23, -1.22, -1.21, -1.20, -1.19, -1.18, -1.17, -1.16, -1.15, -1.14, -1.13, -1.12, -1.11, -1.10, -1.09, -1.08, -1.07)
+CA_TABLE_DEG = (41.514, 44.995, 48.411, 51.920, 55.648, 59.390, 63.290, 67.523, 71.910, 76.604, 81.865, 87.475, 93.742, 100.779, 108.800, 117.996, 128.809, 142.173)
+
+
+def wall_strength_for_angle(angle_deg: float) -> float:
+    """G_w giving the contact angle angle_deg at 0.86 Tc: linear interpolation in the
+    table above (41.5 to 142 degrees)."""
+    return float(np.interp(angle_deg, CA_TABLE_DEG, CA_TABLE_GW))
+
+
 X_PERIODIC, X_INLET_OUTLET = 0, 1
 Y_PERIODIC, Y_WALLS = 0, 1
 
@@ -101,6 +115,20 @@ WORKLOADS = {
     "channel_16384x2048": dict(nx=16384, ny=2048,
                                params=base_params(u_amp=0.03, u_period=10000.0),
                                seed=5, noise=0.01, steps=2000),
+    # the 1024 x 128 channel cut down to 128 x 32 (its own seeded noise)
+    "channel_128x32": dict(nx=128, ny=32, params=base_params(u_amp=0.03, u_period=10000.0),
+                           seed=1, noise=0.01, steps=50000),
+    # the same channels with walls at 0.65 Tc (the cold-wall temperature of Section 3.2),
+    # where the vapour condenses on both walls; the explicit energy update goes unstable
+    # after about 20000 updates as the vapour next to the condensate thins out
+    "cold_1024x128": dict(nx=1024, ny=128,
+                          params=base_params(u_amp=0.03, u_period=10000.0, T_wall_left=0.65,
+                                             T_wall_right=0.65),
+                          seed=1, noise=0.01, steps=15000),
+    "cold_128x32": dict(nx=128, ny=32,
+                        params=base_params(u_amp=0.03, u_period=10000.0, T_wall_left=0.65,
+                                           T_wall_right=0.65),
+                        seed=1, noise=0.01, steps=15000),
     # Section 3.2: condensation on a cold wall under gravity, 100 x 300, periodic in x;
     # the top wall is at 0.65 Tc on its middle half and adiabatic beside it, the bottom
     # wall isothermal at the vapour's 0.86 Tc, gravity 1e-4 toward the bottom, walls

@@ -22,15 +22,17 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def channel_set(n, seed):
-    """Uneven channels: lengths 40..400, widths 8..72, wall strengths and inlet
-    periods drawn from a seeded generator."""
-    u = inputs.uniform01(4 * n, seed).reshape(n, 4)
+def channel_set(n, seed, angles=()):
+    """Uneven channels: lengths 40..400, widths 8..72, contact angles 45..135 degrees
+    (wall strengths from the oracle's G_w -> angle table) and inlet periods drawn from a
+    seeded generator; then one channel for each angle in `angles`."""
+    u = inputs.uniform01(4 * (n + len(angles)), seed).reshape(-1, 4)
     specs = []
-    for k in range(n):
+    for k in range(n + len(angles)):
         nx = int(40 + u[k, 0] * 360)
         ny = int(8 + u[k, 1] * 64)
-        p = inputs.base_params(Gw=-1.2 + 0.1 * u[k, 2], u_amp=0.02,
+        ca = 45.0 + 90.0 * u[k, 2] if k < n else angles[k - n]
+        p = inputs.base_params(Gw=inputs.wall_strength_for_angle(ca), u_amp=0.02,
                                u_period=float(200 + int(1800 * u[k, 3])))
         specs.append((nx, ny, p, inputs.noisy_density(nx, ny, inputs.RHO_V_086, 0.01, seed + k)))
     return specs
@@ -135,10 +137,11 @@ def test_default_tile_height_follows_the_batch_size():
 def test_batch_against_the_oracle(storage):
     """Each lattice of a batch of uneven channels (default tile height) against the FP64
     oracle after 150 updates: within 1e-5 with FP32 storage, within the FP16 bounds of
-    the precision tests with FP16 storage."""
+    the precision tests with FP16 storage.  The batch includes channels at both ends of
+    the contact-angle range of the batch workload (45 and 135 degrees)."""
     import oracle
     from paper_1803_01756_gb300.lattice import Batch, Lattice
-    specs = channel_set(5, seed=60)
+    specs = channel_set(5, seed=60, angles=(45.0, 135.0))
     lats = []
     for nx, ny, p, rho0 in specs:
         lat = Lattice(nx, ny, p, kernel=2, storage=storage)

@@ -122,3 +122,19 @@ def test_contact_angle_increases_with_wall_strength():
         angles.append(contact_angle(rho, 0.5 * (inputs.RHO_V_086 + inputs.RHO_L_086)))
     assert angles[0] < angles[1] < angles[2], angles
     assert angles[0] < 90 < angles[2], angles
+
+
+def test_contact_angle_table_literals_match_the_oracle_table():
+    """The workload generator's G_w -> contact-angle literals are the oracle's table
+    (tests/golden/contact_angle_table.json), monotone and spanning 45-135 degrees."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "contact_angle_table.json")) as fh:
+        tab = json.load(fh)
+    pairs = [(g, a) for g, a in zip(tab["Gw"], tab["angle_deg"]) if a < 179]
+    assert list(inputs.CA_TABLE_GW) == pytest.approx([g for g, _ in pairs], abs=1e-12)
+    assert list(inputs.CA_TABLE_DEG) == pytest.approx([a for _, a in pairs], abs=5e-4)
+    assert all(np.diff(inputs.CA_TABLE_DEG) > 0)
+    assert inputs.CA_TABLE_DEG[0] < 45 and inputs.CA_TABLE_DEG[-1] > 135
+    # the table agrees with the ordering pin above: 90 degrees between -1.2 and -1.1
+    assert -1.2 < inputs.wall_strength_for_angle(90.0) < -1.1
