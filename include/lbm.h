@@ -244,9 +244,20 @@ int lbm_batch_set_graph(lbm_batch_h b, int enable);
    1 row compete, with row steps slower the more tiles share an SM.  A launch has one CTA
    per tile when there are fewer tiles than resident CTAs. */
 int lbm_batch_set_tile_rows(lbm_batch_h b, int rows);
-/* Time tile heights 16..128 rows with steps_per_candidate timed updates each (plus two
-   warm-up updates) and keep the fastest.  These are real updates: every lattice
-   advances by 7 * (steps_per_candidate + 2) steps.  Synchronises the stream. */
+/* Set the tiling: output rows and columns per tile and lattice columns per thread (1, or 2
+   when the batch's modes include the energy equation and the pseudopotential forces; cols
+   at most 118 with one column per thread, an even number up to 244 with two).
+   LBM_ERR_ARG otherwise.  Results do not depend on the tiling. */
+int lbm_batch_set_tiling(lbm_batch_h b, int rows, int cols, int cols_per_thread);
+int lbm_batch_tiling(lbm_batch_h b, int *rows, int *cols, int *cols_per_thread);
+/* The library's autotuner: times tilings with steps_per_candidate timed updates each (plus
+   two warm-up updates) and keeps the fastest.  Candidates: tile heights 16, 24, 32, 48, 64,
+   96 and 128 rows at the widest tiles, for one column per thread and, where the modes allow
+   it, two; then tiles of three quarters and half that width at the winner's height and
+   column count.  These are real updates: every lattice advances by
+   (7 k + 2) * (steps_per_candidate + 2) steps, k the number of column counts tried (1 or 2).
+   Writes the winning height to *best_rows (may be NULL; lbm_batch_tiling gives all three).
+   Synchronises the stream. */
 int lbm_batch_autotune(lbm_batch_h b, int steps_per_candidate, int *best_rows, void *stream);
 int lbm_batch_info(lbm_batch_h b, int *ntiles, int *grid, int *tile_rows);
 /* Synchronises the device, frees the batch's tables; the lattices are untouched. */

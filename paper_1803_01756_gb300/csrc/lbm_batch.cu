@@ -16,6 +16,9 @@ struct lbm_batch {
   lbm::DevParams mode{};  // boundary modes and physics switches shared by all lattices
   std::vector<lbm_lattice *> lat;  // work-list order: most tiles first
   int tile_rows = 64;              // output rows per tile (default_rows, or set / autotuned)
+  int tile_cols = 0;               // output columns per tile (even with two columns per thread)
+  int cpt = 1;                     // lattice columns per thread of the batched kernel
+  int grid_of[3] = {0, 0, 0};      // resident CTAs with 1 and 2 columns per thread (0: none)
   int ntiles = 0, grid = 0, sms = 1;
   BatchChannel *d_ch[2] = {nullptr, nullptr};  // tables for even and odd steps of a call
   std::vector<BatchChannel> h_ch[2];
@@ -36,10 +39,9 @@ namespace {
 
 using lbm_host::cuda_fail;
 
-int tiles_of(const lbm_lattice *h, int rows) {
-  const int W = lbm::fused_max_width(1);
+int tiles_of(const lbm_lattice *h, int rows, int cols) {
   const int H = std::min(rows, h->ny);
-  return ((h->nx + W - 1) / W) * ((h->ny + H - 1) / H);
+  return ((h->nx + cols - 1) / cols) * ((h->ny + H - 1) / H);
 }
 
 void drop_graph(lbm_batch *b) {
@@ -52,10 +54,12 @@ void drop_graph(lbm_batch *b) {
 // Work-list layout for the current tile height: lattices with the most work first
 void layout(lbm_batch *b) {
   std::stable_sort(b->lat.begin(), b->lat.end(), [&](const lbm_lattice *x, const lbm_lattice *y) {
-    return (long long)tiles_of(x, b->tile_rows) * x->nx > (long long)tiles_of(y, b->tile_rows) * y->nx;
+    return (long long)tiles_of(x, b->tile_rows, b->tile_cols) * x->nx >
+           (long long)tiles_of(y, b->tile_rows, b->tile_cols) * y->nx;
   });
   b->ntiles = 0;
-  for (auto *h : b->lat) b->ntiles += tiles_of(h, b->tile_rows);
+  for (auto *h : b->lat) b->ntiles += tiles_of(h, b->tile_rows, b->tile_cols);
+  b->grid = b->grid_of[b->cpt];
   drop_graph(b);
 }
 
@@ -64,7 +68,7 @@ void layout(lbm_batch *b) {
 // returns the makespan in row steps and the number of tiles.
 double schedule(const lbm_batch *b, const std::vector<const lbm_lattice *> &order, int H,
                 long long &ntiles) {
-  const int W = lbm::fused_max_width(1);
+  const int W = b->tile_cols;
   std::priority_queue<double, std::vector<double>, std::greater<double>> slots;
   for (int k = 0; k < b->grid; k++) slots.push(0.0);
   double makespan = 0.0;
@@ -134,7 +138,7 @@ int default_rows(const lbm_batch *b) {
 // Channel tables for the lattices' current buffers: table 0 for steps at even
 // offsets from now, table 1 for odd offsets.
 int upload_tables(lbm_batch *b, cudaStream_t s) {
-  const int W = lbm::fused_max_width(1);
+  const int W = b->tile_cols;
   int begin = 0;
   for (int par = 0; par < 2; par++) b->h_ch[par].resize(b->lat.size());
   for (size_t i = 0; i < b->lat.size(); i++) {
@@ -155,7 +159,7 @@ int upload_tables(lbm_batch *b, cudaStream_t s) {
       c.strips = (h->nx + W - 1) / W;
       c.tile_begin = begin;
     }
-    begin += tiles_of(h, b->tile_rows);
+    begin += tiles_of(h, b->tile_rows, b->tile_cols);
   }
   const size_t bytes = sizeof(BatchChannel) * b->lat.size();
   for (int par = 0; par < 2; par++)
@@ -168,7 +172,7 @@ int launch_grid(const lbm_batch *b) { return std::min(b->grid, b->ntiles); }
 
 int launch_one(lbm_batch *b, int k, cudaStream_t s) {
   const int n = (int)b->lat.size();
-  return cuda_fail(lbm::launch_fused_batch(b->mode, b->storage, b->d_ch[k & 1], n,
+  return cuda_fail(lbm::launch_fused_batch(b->mode, b->storage, b->cpt, b->d_ch[k & 1], n,
                                            b->d_sc + (size_t)k * n, b->ntiles, b->d_counter,
                                            launch_grid(b), s));
 }
@@ -224,7 +228,10 @@ int lbm_batch_create(lbm_h *lattices, int n, lbm_batch_h *out) {
   b->mode = first->dp;
   b->lat.assign(lattices, lattices + n);
   cudaError_t e = cudaSetDevice(b->device);
-  b->grid = e == cudaSuccess ? lbm::fused_batch_grid(b->mode, b->storage, b->device) : 0;
+  for (int c = 1; c <= 2 && e == cudaSuccess; c++)
+    b->grid_of[c] = lbm::fused_batch_grid(b->mode, b->storage, c, b->device);
+  b->grid = b->grid_of[1];
+  b->tile_cols = lbm::fused_batch_width(1);
   if (b->grid > 0 &&
       cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
     b->grid = 0;
@@ -286,7 +293,7 @@ int lbm_batch_step(lbm_batch_h b, long nsteps, void *stream) {
       for (int k = 0; k < m; k++) {
         // k-th step of this chunk runs with the table of its parity in the call
         const int par = (phase + k) & 1;
-        rc = cuda_fail(lbm::launch_fused_batch(b->mode, b->storage, b->d_ch[par], n,
+        rc = cuda_fail(lbm::launch_fused_batch(b->mode, b->storage, b->cpt, b->d_ch[par], n,
                                                b->d_sc + (size_t)k * n, b->ntiles, b->d_counter,
                                                launch_grid(b), s));
         if (rc) return rc;
@@ -319,42 +326,90 @@ int lbm_batch_set_tile_rows(lbm_batch_h b, int rows) {
   return LBM_OK;
 }
 
+int lbm_batch_set_tiling(lbm_batch_h b, int rows, int cols, int cols_per_thread) {
+  if (!b || rows < 1 || cols < 1) return LBM_ERR_ARG;
+  if (cols_per_thread != 1 && cols_per_thread != 2) return LBM_ERR_ARG;
+  if (b->grid_of[cols_per_thread] < 1) return LBM_ERR_ARG;
+  if (cols > lbm::fused_batch_width(cols_per_thread)) return LBM_ERR_ARG;
+  if (cols_per_thread == 2 && (cols & 1)) return LBM_ERR_ARG;
+  b->tile_rows = rows;
+  b->tile_cols = cols;
+  b->cpt = cols_per_thread;
+  layout(b);
+  return LBM_OK;
+}
+
+int lbm_batch_tiling(lbm_batch_h b, int *rows, int *cols, int *cols_per_thread) {
+  if (!b) return LBM_ERR_ARG;
+  if (rows) *rows = b->tile_rows;
+  if (cols) *cols = b->tile_cols;
+  if (cols_per_thread) *cols_per_thread = b->cpt;
+  return LBM_OK;
+}
+
 int lbm_batch_autotune(lbm_batch_h b, int steps_per_candidate, int *best_rows, void *stream) {
   if (!b || steps_per_candidate < 2) return LBM_ERR_ARG;
   LBM_CUDA(cudaSetDevice(b->device));
   cudaStream_t s = (cudaStream_t)stream;
-  static const int candidates[] = {16, 24, 32, 48, 64, 96, 128};
+  struct Cand {
+    int rows, cols, cpt;
+  };
+  static const int heights[] = {16, 24, 32, 48, 64, 96, 128};
   cudaEvent_t e0, e1;
   LBM_CUDA(cudaEventCreate(&e0));
   LBM_CUDA(cudaEventCreate(&e1));
   const bool graph = b->use_graph;
   b->use_graph = false;
   float best = -1.0f;
-  int best_h = b->tile_rows;
+  Cand win{b->tile_rows, b->tile_cols, b->cpt};
   int rc = LBM_OK;
-  for (int H : candidates) {
-    b->tile_rows = H;
+  auto time_one = [&](const Cand &c) -> int {
+    b->tile_rows = c.rows;
+    b->tile_cols = c.cols;
+    b->cpt = c.cpt;
     layout(b);
-    rc = lbm_batch_step(b, 2, stream);  // warm-up
-    if (rc) break;
+    int r = lbm_batch_step(b, 2, stream);  // warm-up
+    if (r) return r;
     LBM_CUDA(cudaEventRecord(e0, s));
-    rc = lbm_batch_step(b, steps_per_candidate, stream);
-    if (rc) break;
+    r = lbm_batch_step(b, steps_per_candidate, stream);
+    if (r) return r;
     LBM_CUDA(cudaEventRecord(e1, s));
     LBM_CUDA(cudaEventSynchronize(e1));
     float ms = 0.0f;
     LBM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     if (best < 0.0f || ms < best) {
       best = ms;
-      best_h = H;
+      win = c;
+    }
+    return LBM_OK;
+  };
+  // tile heights at the widest tiles, for each column count the mode has a kernel for
+  for (int cpt = 1; cpt <= 2 && rc == LBM_OK; cpt++) {
+    if (b->grid_of[cpt] < 1) continue;
+    for (int H : heights) {
+      rc = time_one(Cand{H, lbm::fused_batch_width(cpt), cpt});
+      if (rc) break;
+    }
+  }
+  // then narrower tiles (three quarters and half the width) at the winner's height
+  if (rc == LBM_OK) {
+    const Cand base = win;
+    const int Wmax = lbm::fused_batch_width(base.cpt);
+    for (int num : {3, 2}) {
+      int W = Wmax * num / 4;
+      if (base.cpt == 2) W &= ~1;
+      rc = time_one(Cand{base.rows, W, base.cpt});
+      if (rc) break;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->use_graph = graph;
-  b->tile_rows = best_h;
+  b->tile_rows = win.rows;
+  b->tile_cols = win.cols;
+  b->cpt = win.cpt;
   layout(b);
-  if (best_rows) *best_rows = best_h;
+  if (best_rows) *best_rows = win.rows;
   return rc;
 }
 

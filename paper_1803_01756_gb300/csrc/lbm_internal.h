@@ -58,13 +58,17 @@ cudaError_t fused_c2_launch(const DevParams &p, int storage, const void *gs, voi
                             dim3 grid, cudaStream_t s);
 
 // batched fused path: a persistent grid of `grid` CTAs walks the tiles of nch
-// lattices (all with the modes of `mode` and storage `storage`); counter: two ints,
-// zero before the first launch, left at zero by every launch
-cudaError_t launch_fused_batch(const DevParams &mode, int storage, const BatchChannel *ch, int nch,
-                               const StepScalars *sc, int ntiles, int *counter, int grid,
+// lattices (all with the modes of `mode` and storage `storage`) with cpt lattice columns
+// per thread (2: even tile widths); counter: two ints, zero before the first launch, left
+// at zero by every launch
+cudaError_t launch_fused_batch(const DevParams &mode, int storage, int cpt, const BatchChannel *ch,
+                               int nch, const StepScalars *sc, int ntiles, int *counter, int grid,
                                cudaStream_t s);
-// resident CTAs of the batched kernel on this device (0 on failure)
-int fused_batch_grid(const DevParams &mode, int storage, int device);
+// resident CTAs of the batched kernel with cpt columns per thread on this device (0 on
+// failure, and for cpt = 2 in modes without the energy equation or the pseudopotential)
+int fused_batch_grid(const DevParams &mode, int storage, int cpt, int device);
+// output columns of one CTA of the batched kernel with cpt columns per thread
+int fused_batch_width(int cpt);
 
 // set-up and reductions
 cudaError_t launch_init(const DevParams &p, int storage, const double *rho0, void *gout,

@@ -110,6 +110,9 @@ SIGNATURES = {
     "lbm_batch_set_graph": ([_vp, ctypes.c_int], ctypes.c_int),
     "lbm_batch_set_tile_rows": ([_vp, ctypes.c_int], ctypes.c_int),
     "lbm_batch_autotune": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp], ctypes.c_int),
+    "lbm_batch_set_tiling": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "lbm_batch_tiling": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lbm_batch_info": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                         ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "lbm_batch_destroy": ([_vp], None),
@@ -363,7 +366,15 @@ class Batch:
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(self._lib.lbm_batch_info(self._h, ctypes.byref(a), ctypes.byref(b),
                                         ctypes.byref(c)), "lbm_batch_info")
-        return {"tiles": a.value, "grid": b.value, "tile_rows": c.value}
+        r, w, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.lbm_batch_tiling(self._h, ctypes.byref(r), ctypes.byref(w),
+                                          ctypes.byref(k)), "lbm_batch_tiling")
+        return {"tiles": a.value, "grid": b.value, "tile_rows": c.value, "tile_cols": w.value,
+                "cols_per_thread": k.value}
+
+    def set_tiling(self, rows: int, cols: int, cols_per_thread: int = 1):
+        _check(self._lib.lbm_batch_set_tiling(self._h, int(rows), int(cols),
+                                              int(cols_per_thread)), "lbm_batch_set_tiling")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -50,8 +50,12 @@ def run_alone(specs, steps):
     return out
 
 
-@pytest.mark.parametrize("graph,tile_rows", [(False, 64), (True, 24), (False, 7)])
-def test_batch_equals_alone(graph, tile_rows):
+@pytest.mark.parametrize("graph,tile_rows,tiling", [(False, 64, None), (True, 24, None),
+                                                    (False, 7, None), (False, 0, (24, 94, 1)),
+                                                    (True, 0, (16, 244, 2)),
+                                                    (False, 0, (40, 120, 2))])
+def test_batch_equals_alone(graph, tile_rows, tiling):
+    """Default tilings, narrower tiles and two lattice columns per thread."""
     from paper_1803_01756_gb300.lattice import Batch, Lattice
     specs = channel_set(12, seed=30)
     steps = 37  # two graph chunks of 16 and a partial chunk of odd length
@@ -61,7 +65,11 @@ def test_batch_equals_alone(graph, tile_rows):
         lat = Lattice(nx, ny, p, kernel=2)
         lat.write_fields(rho0)
         lats.append(lat)
-    b = Batch(lats, graph=graph, tile_rows=tile_rows)
+    b = Batch(lats, graph=graph, tile_rows=tile_rows or None)
+    if tiling:
+        b.set_tiling(*tiling)
+        info = b.info()
+        assert (info["tile_rows"], info["tile_cols"], info["cols_per_thread"]) == tiling
     b.step(steps)
     for lat, ref in zip(lats, alone):
         assert lat.t == steps
@@ -98,9 +106,14 @@ def test_autotune_picks_a_candidate_and_keeps_results_finite():
         lats.append(lat)
     b = Batch(lats)
     best = b.autotune(3)
+    info = b.info()
     assert best in (16, 24, 32, 48, 64, 96, 128)
-    assert b.info()["tile_rows"] == best
-    assert all(lat.t == 7 * 5 for lat in lats)
+    assert info["tile_rows"] == best
+    # two column counts are tried for this mode: 7 heights each, then two widths
+    assert all(lat.t == (7 * 2 + 2) * 5 for lat in lats)
+    assert info["cols_per_thread"] in (1, 2)
+    widths = {1: (118, 88, 59), 2: (244, 182, 122)}[info["cols_per_thread"]]
+    assert info["tile_cols"] in widths
     for lat in lats:
         assert all(np.isfinite(a).all() for a in lat.read_fields())
     b.close()
@@ -162,3 +175,23 @@ def test_batch_against_the_oracle(storage):
         assert np.hypot(ux - rux, uy - ruy).max() <= tol["u"] * max(np.hypot(rux, ruy).max(), 1e-3)
         assert np.abs(T - rT).max() <= tol["T"] * np.abs(rT).max()
         lat.close()
+
+
+def test_batch_tiling_is_validated():
+    """Two columns per thread need even tile widths up to 244 and the modes with the
+    energy equation and the pseudopotential; one column allows widths up to 118."""
+    from paper_1803_01756_gb300.lattice import Batch, Lattice, LbmError
+    a = Lattice(64, 16, inputs.base_params(), kernel=2)
+    b = Batch([a])
+    for bad in [(16, 119, 1), (16, 245, 2), (16, 101, 2), (0, 64, 1), (16, 64, 3)]:
+        with pytest.raises(LbmError):
+            b.set_tiling(*bad)
+    b.set_tiling(16, 244, 2)
+    b.close()
+    a.close()
+    c = Lattice(64, 16, inputs.base_params(thermal=0), kernel=2)
+    b = Batch([c])
+    with pytest.raises(LbmError):
+        b.set_tiling(16, 64, 2)
+    b.close()
+    c.close()

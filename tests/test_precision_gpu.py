@@ -25,6 +25,17 @@ CHANNEL_BOUNDS = {
 }
 
 
+# equimolar radius of the sessile drop (about 14 nodes) against the oracle's, in nodes
+# (measured on GB300: f32 2.9e-4, f16 5.5e-2, bf16 0.19)
+RADIUS_BOUNDS = {"f32": 1e-3, "f16": 0.1, "bf16": 0.4}
+# the 4096 x 512 benchmark channel's parameters on a 128 x 32 cut, 20000 updates
+# (measured on GB300: f32 1.2e-6 / 2.0e-6 / 1.9e-7, f16 1.0e-3 / 2.1e-3 / 1.3e-4,
+#  bf16 3.4e-2 / 0.31 / 3.2e-3 for rho / u / T)
+LONG_BOUNDS = {"f32": {"rho": 1e-5, "u": 1e-5, "T": 1e-5},
+               "f16": {"rho": 3e-3, "u": 1e-2, "T": 5e-4},
+               "bf16": {"rho": 0.1, "u": 0.6, "T": 1e-2}}
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _cuda():
     torch = pytest.importorskip("torch")
@@ -83,6 +94,13 @@ def contact_angle(rho):
     return ca(rho, 0.5 * (inputs.RHO_V_086 + inputs.RHO_L_086))
 
 
+def equimolar_radius(rho):
+    """Radius of the half-disc holding the drop's condensed mass at liquid density:
+    sqrt(2 A / pi), A = sum(rho - rho_v) / (rho_l - rho_v)."""
+    A = (rho - inputs.RHO_V_086).sum() / (inputs.RHO_L_086 - inputs.RHO_V_086)
+    return float(np.sqrt(2 * A / np.pi))
+
+
 @pytest.fixture(scope="module")
 def drop_reference():
     p = inputs.base_params(thermal=0, x_bc=0, y_bc=1, Gw=-1.15)
@@ -109,11 +127,13 @@ def test_liquid_drop_density_and_contact_angle(storage, drop_reference):
     lat.close()
     err = np.abs(rho - rho_ref).max() / rho_ref.max()
     ca = contact_angle(rho)
+    dr = abs(equimolar_radius(rho) - equimolar_radius(rho_ref))
     print(f"\nsessile drop, {storage}: rho error {err:.2e}, contact angle {ca:.2f} "
-          f"(oracle {ca_ref:.2f})")
+          f"(oracle {ca_ref:.2f}), equimolar radius error {dr:.2e}")
     bound = {"f32": 2e-4, "f16": 8e-2, "bf16": 0.25}[storage]
     assert err <= bound
     assert abs(ca - ca_ref) <= {"f32": 0.01, "f16": 0.5, "bf16": 6.0}[storage]
+    assert dr <= RADIUS_BOUNDS[storage], (storage, dr)
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
@@ -134,3 +154,34 @@ def test_16bit_checkpoint_round_trip(storage):
         assert np.array_equal(x, y)
     a.close()
     b.close()
+
+
+@pytest.fixture(scope="module")
+def long_reference():
+    """FP64 oracle on a 128 x 32 cut of the 4096 x 512 benchmark channel (its parameters
+    and noise seed), 20000 updates (about 40 s of host time)."""
+    w = inputs.workload("channel_4096x512")
+    rho0 = inputs.noisy_density(128, 32, inputs.RHO_V_086, w["noise"], w["seed"])
+    o = oracle.Oracle(128, 32, w["params"])
+    o.set_fields(rho0)
+    o.step(20000)
+    assert o.status == 0
+    return w["params"], rho0, o.fields()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_benchmark_channel_20000_updates(storage, long_reference):
+    """The benchmark channel's parameters over its 20000 updates, on a 128 x 32 cut that
+    the oracle finishes in about 40 s: errors of rho, u and T per storage format."""
+    from paper_1803_01756_gb300.lattice import Lattice
+    p, rho0, ref = long_reference
+    lat = Lattice(128, 32, p, storage=STORAGES[storage])
+    lat.write_fields(rho0)
+    lat.step(20000)
+    err = errors(lat.read_fields(), ref)
+    assert lat.status() == 0
+    lat.close()
+    print(f"\n128x32 cut of the 4096x512 channel, 20000 updates, {storage}: " +
+          ", ".join(f"{k} {v:.2e}" for k, v in err.items()))
+    for k, bound in LONG_BOUNDS[storage].items():
+        assert err[k] <= bound, (storage, err)
