@@ -269,9 +269,12 @@ void lbm_batch_destroy(lbm_batch_h b);
    and queue first come, first served.  The worker admits queued jobs while fewer
    than max_active run and their device footprint (populations, temperature and
    scratch of lbm_create) fits in hbm_budget bytes; it then advances all running
-   jobs that share modes together in batched launches (lbm_batch_*), chunk_steps
-   updates per round (fewer when a job has fewer left), reads finished jobs' fields
-   back to host memory and frees their device memory, which admits the next jobs.
+   jobs that share modes together in batched launches (lbm_batch_*; a group's batch is
+   kept across rounds while its jobs stay the same), and each job of 2^20 nodes or more,
+   which fills the GPU alone, with lbm_step, chunk_steps updates per round (fewer when a
+   job has fewer left); it reads every job's status word with one synchronisation, reads
+   finished jobs' fields back to host memory and frees their device memory, which admits
+   the next jobs.
    A job's fields equal those of the same job run alone (lbm_step) within the FP32
    parity bound. */
 #define LBM_JOB_QUEUED 0

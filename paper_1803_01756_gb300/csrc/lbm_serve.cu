@@ -53,6 +53,14 @@ struct lbm_server {
   bool stop = false;
   std::thread worker;
   cudaStream_t stream = nullptr;
+  // batched launch of each mode group, kept across rounds while the group's jobs (by id)
+  // stay the same; rebuilt when a job joins or leaves
+  struct Group {
+    std::vector<long> ids;
+    lbm_batch_h b = nullptr;
+  };
+  std::map<int, Group> groups;
+  unsigned *h_status = nullptr;  // pinned, one status word per active job
 };
 
 namespace {
@@ -123,23 +131,69 @@ void admit(lbm_server *s) {
   }
 }
 
+void drop_group(lbm_server::Group &g) {
+  if (g.b) lbm_batch_destroy(g.b);
+  g.b = nullptr;
+  g.ids.clear();
+}
+
 // One scheduling round: every group of active jobs with equal modes advances by the
-// same number of steps in batched launches; finished jobs are read back and freed.
+// same number of steps in one batched launch per step; then every job's status word is
+// read with one synchronisation, and finished jobs are read back and freed.
+// A lattice this large fills the GPU alone (about 4 tiles of the fused kernel per SM) and
+// runs faster in the single-lattice kernel than in the batched one (69 against 102 us per
+// update on 4096 x 512), so it is stepped alone.
+constexpr long long kAloneNodes = 1LL << 20;
+
 void round(lbm_server *s) {
   std::map<int, std::vector<std::shared_ptr<Job>>> groups;
-  for (auto &j : s->active) groups[mode_key(j->lat)].push_back(j);
+  std::vector<std::shared_ptr<Job>> alone;
+  for (auto &j : s->active) {
+    if ((long long)j->nx * j->ny >= kAloneNodes)
+      alone.push_back(j);
+    else
+      groups[mode_key(j->lat)].push_back(j);
+  }
+  for (auto &j : alone) {
+    const long m = std::min(s->cfg.chunk_steps, j->nsteps - j->done_steps);
+    if (m <= 0) continue;
+    const int rc = lbm_step(j->lat, m, s->stream);
+    s->launches += m;
+    if (rc != LBM_OK)
+      retire(s, j, rc);
+    else
+      j->done_steps += m;
+  }
+  // cached batches whose group changed or vanished go first
+  for (auto it = s->groups.begin(); it != s->groups.end();) {
+    auto g = groups.find(it->first);
+    bool same = g != groups.end() && g->second.size() == it->second.ids.size();
+    for (size_t k = 0; same && k < g->second.size(); k++) same = g->second[k]->id == it->second.ids[k];
+    if (same) {
+      ++it;
+    } else {
+      drop_group(it->second);
+      it = s->groups.erase(it);
+    }
+  }
   for (auto &kv : groups) {
     auto &g = kv.second;
     long m = s->cfg.chunk_steps;
     for (auto &j : g) m = std::min(m, j->nsteps - j->done_steps);
     if (m <= 0) continue;
-    std::vector<lbm_h> hs;
-    for (auto &j : g) hs.push_back(j->lat);
-    lbm_batch_h b = nullptr;
-    int rc = lbm_batch_create(hs.data(), (int)hs.size(), &b);
-    if (rc == LBM_OK) rc = lbm_batch_step(b, m, s->stream);
-    if (b) lbm_batch_destroy(b);
+    lbm_server::Group &cached = s->groups[kv.first];
+    int rc = LBM_OK;
+    if (!cached.b) {
+      std::vector<lbm_h> hs;
+      for (auto &j : g) {
+        hs.push_back(j->lat);
+        cached.ids.push_back(j->id);
+      }
+      rc = lbm_batch_create(hs.data(), (int)hs.size(), &cached.b);
+    }
+    if (rc == LBM_OK) rc = lbm_batch_step(cached.b, m, s->stream);
     s->launches += m;
+    if (rc != LBM_OK) drop_group(cached);
     for (auto &j : g) {
       if (rc != LBM_OK) {
         retire(s, j, rc);
@@ -148,13 +202,22 @@ void round(lbm_server *s) {
       j->done_steps += m;
     }
   }
-  cudaStreamSynchronize(s->stream);
+  // status words of the running jobs: one asynchronous copy each, one synchronisation
+  std::vector<std::shared_ptr<Job>> run;
+  for (auto &j : s->active)
+    if (j->state == LBM_JOB_RUNNING) run.push_back(j);
+  bool copied = true;
+  for (size_t k = 0; k < run.size(); k++)
+    copied = copied && cudaMemcpyAsync(&s->h_status[k], run[k]->lat->status, sizeof(unsigned),
+                                       cudaMemcpyDeviceToHost, s->stream) == cudaSuccess;
+  copied = cudaStreamSynchronize(s->stream) == cudaSuccess && copied;
   std::vector<std::shared_ptr<Job>> still;
-  for (auto &j : s->active) {
-    if (j->state != LBM_JOB_RUNNING) continue;  // retired above
-    unsigned bits = 0;
-    lbm_status(j->lat, &bits, 0, s->stream);
-    if (bits) {
+  for (size_t k = 0; k < run.size(); k++) {
+    auto &j = run[k];
+    const unsigned bits = copied ? s->h_status[k] : ~0u;
+    if (!copied) {
+      retire(s, j, LBM_ERR_CUDA);
+    } else if (bits) {
       retire(s, j, LBM_ERR_UNSTABLE);
     } else if (j->done_steps >= j->nsteps) {
       retire(s, j, LBM_JOB_DONE);
@@ -180,6 +243,8 @@ void serve(lbm_server *s) {
     if (!s->active.empty()) round(s);
   }
   // stopped: jobs still running are cancelled
+  for (auto &kv : s->groups) drop_group(kv.second);
+  s->groups.clear();
   for (auto &j : s->active) retire(s, j, LBM_ERR_ARG);
   s->active.clear();
 }
@@ -199,6 +264,12 @@ int lbm_server_create(const lbm_server_config_t *cfg, lbm_server_h *out) {
       cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete s;
     return LBM_ERR_CUDA;
+  }
+  if (cudaMallocHost((void **)&s->h_status, sizeof(unsigned) * (size_t)cfg->max_active) !=
+      cudaSuccess) {
+    cudaStreamDestroy(s->stream);
+    delete s;
+    return LBM_ERR_OOM;
   }
   s->worker = std::thread(serve, s);
   *out = s;
@@ -285,6 +356,7 @@ void lbm_server_destroy(lbm_server_h s) {
   }
   if (s->worker.joinable()) s->worker.join();
   cudaStreamDestroy(s->stream);
+  cudaFreeHost(s->h_status);
   delete s;
 }
 
