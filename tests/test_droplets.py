@@ -124,3 +124,16 @@ def test_library_rejects_bad_arguments(lib_stats):
     from paper_1803_01756_gb300.lattice import LbmError
     with pytest.raises(LbmError):
         lib_stats(np.zeros((4, 4)), float("nan"), 0.0)
+
+
+@pytest.mark.parametrize("theta", [50.0, 90.0, 130.0])
+def test_oracle_contact_angle_of_synthetic_caps(theta):
+    """A circular cap of radius R meeting the wall (y = -1/2) at angle theta, drawn with a
+    smooth tanh interface: the measure 2 atan(2h / w) returns theta within 2 degrees."""
+    from oracle.droplets import contact_angle
+    nx, ny, R = 160, 80, 22.0
+    yc = -0.5 - R * np.cos(np.radians(theta))
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    r = np.hypot(x - nx / 2, y - yc)
+    rho = RV + (RL - RV) * 0.5 * (1 - np.tanh((r - R) / 1.5))
+    assert contact_angle(rho, THR) == pytest.approx(theta, abs=2.0)
