@@ -223,45 +223,38 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
   // written one row step earlier, at the bottom row 0 writes its value into the slot of
   // row -1 (not read by any stage before then).  Adiabatic columns come with periodic x
   // (lbm_create accepts them only then: compile-time false for open x).
+  // per-column cases as bits of one register per column (the kernel runs at its register
+  // bound): FL_IN / FL_OUT ghost beyond the inlet / outlet, FL_OUTC output column, FL_MIR /
+  // FL_MIN0 the boundary column that mirrors into the outlet / inlet ghost slot (FL_MIN:
+  // also the velocity, pressure inlet), FL_ADB / FL_ADT adiabatic bottom / top wall column
+  enum : unsigned { FL_IN = 1u, FL_OUT = 2u, FL_OUTC = 4u, FL_MIR = 8u, FL_MIN0 = 16u,
+                    FL_MIN = 32u, FL_ADB = 64u, FL_ADT = 128u };
   int cx[CPT];
-  bool col_in[CPT], col_out[CPT], ghost[CPT], outc[CPT], mirror[CPT], mirror_in0[CPT],
-      mirror_in[CPT], adi_bot[CPT], adi_top[CPT];
-  bool wS0[CPT], wU[CPT], wT[CPT];  // the column writes its own slot in S0, S1 (u), S2-S4
-  float twall[CPT], twall_top[CPT];
+  unsigned fl[CPT];
   // Pull offsets relative to the node's own index (Eq. 12, f_i(x) = f*_i(x - e_i)), used
   // on every row not next to a wall.  Next to a periodic seam the source column wraps;
   // at an open end the populations entering from outside (Zou-He unknowns) read any
   // in-bounds element of their plane and are replaced by pull_fix.
   int poff[CPT][9];
   unsigned unk_edge[CPT];
-  bool allS0 = true, allU = true, allT = true;
 #pragma unroll
   for (int k = 0; k < CPT; k++) {
     const int c = c0 + k, lc = CPT * t + k;
-    col_in[k] = false;
-    col_out[k] = false;
+    unsigned f = 0u;
     if (!XO) {
       cx[k] = modi(c, pg.nx);
     } else {
-      col_in[k] = c < 0;
-      col_out[k] = c >= pg.nx;
+      f |= c < 0 ? FL_IN : 0u;
+      f |= c >= pg.nx ? FL_OUT : 0u;
       cx[k] = min(max(c, 0), pg.nx - 1);
     }
-    outc[k] = c >= X0 && c < xe;
-    ghost[k] = col_in[k] || col_out[k];
-    mirror[k] = XO && c == pg.nx - 1 && lc + 1 < NC;
-    mirror_in0[k] = XO && c == 0 && lc >= 1;
-    mirror_in[k] = mirror_in0[k] && pg.p_inlet;
-    twall[k] = wall_T_dev(pg, cx[k]);
-    twall_top[k] = wall_T_top_dev(pg, cx[k]);
-    adi_bot[k] = YW && !XO && pg.adiabatic && wall_adiabatic(pg, cx[k], false);
-    adi_top[k] = YW && !XO && pg.adiabatic && wall_adiabatic(pg, cx[k], true);
-    wS0[k] = !ghost[k];
-    wU[k] = !col_out[k] && !(col_in[k] && pg.p_inlet);
-    wT[k] = !col_out[k];
-    allS0 = allS0 && wS0[k];
-    allU = allU && wU[k];
-    allT = allT && wT[k];
+    f |= c >= X0 && c < xe ? FL_OUTC : 0u;
+    f |= XO && c == pg.nx - 1 && lc + 1 < NC ? FL_MIR : 0u;
+    f |= XO && c == 0 && lc >= 1 ? FL_MIN0 : 0u;
+    f |= XO && c == 0 && lc >= 1 && pg.p_inlet ? FL_MIN : 0u;
+    f |= YW && !XO && pg.adiabatic && wall_adiabatic(pg, cx[k], false) ? FL_ADB : 0u;
+    f |= YW && !XO && pg.adiabatic && wall_adiabatic(pg, cx[k], true) ? FL_ADT : 0u;
+    fl[k] = f;
     unk_edge[k] = 0u;
 #pragma unroll
     for (int i = 0; i < 9; i++) {
@@ -275,6 +268,24 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
       }
     }
   }
+#define HAS(k, b) ((fl[k] & (b)) != 0u)
+  // the column writes its own ring slot in S0 (not a ghost), in S1's velocity ring (not
+  // the outlet ghost, not the pressure inlet's ghost) and in the stage rings (not the
+  // outlet ghost); wall temperatures are formed where a wall row needs them
+  bool wS0[CPT], wU[CPT], wT[CPT], outc[CPT];
+  bool allS0 = true, allU = true, allT = true;
+#pragma unroll
+  for (int k = 0; k < CPT; k++) {
+    wS0[k] = !HAS(k, FL_IN | FL_OUT);
+    wU[k] = !HAS(k, FL_OUT) && !(HAS(k, FL_IN) && pg.p_inlet);
+    wT[k] = !HAS(k, FL_OUT);
+    outc[k] = HAS(k, FL_OUTC);
+    allS0 = allS0 && wS0[k];
+    allU = allU && wU[k];
+    allT = allT && wT[k];
+  }
+#define TWALL(k) wall_T_dev(pg, cx[k])
+#define TWALL_TOP(k) wall_T_top_dev(pg, cx[k])
   // the CTA holds a column of an open end (uniform over the CTA): only such CTAs have
   // Zou-He unknowns to fix
   const bool xb = XO && (X0 - FH <= 0 || X0 - FH + NC - 1 >= pg.nx - 1);
@@ -368,10 +379,10 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
           const typename ST::T *src = gs + own;
 #pragma unroll
           for (int i = 0; i < 9; i++) fc[k][i] = ST::load(src + poff[k][i], i);
-          unk[k] = ghost[k] ? 0u : unk_edge[k];
+          unk[k] = HAS(k, FL_IN | FL_OUT) ? 0u : unk_edge[k];
         } else {
           pull_load<ST>(pg, gs, cx[k], ry, fc[k], unk[k]);
-          if (ghost[k]) unk[k] = 0u;
+          if (HAS(k, FL_IN | FL_OUT)) unk[k] = 0u;
         }
         Tc[k] = __ldg(Tin + own);
       }
@@ -484,12 +495,12 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
             float2 uu[CPT];
 #pragma unroll
             for (int k = 0; k < CPT; k++)
-              uu[k] = col_in[k] ? make_float2(sc.u_in, 0.0f) : make_float2(ux[k], uy[k]);
+              uu[k] = HAS(k, FL_IN) ? make_float2(sc.u_in, 0.0f) : make_float2(ux[k], uy[k]);
             ring_put2<CPT>(ring_u, sl, uu, allU, wU);
 #pragma unroll
             for (int k = 0; k < CPT; k++) {
-              if (mirror[k]) F2(ring_u, sl + 4 * k + 4) = uu[k];
-              if (mirror_in[k]) F2(ring_u, sl + 4 * k - 4) = uu[k];
+              if (HAS(k, FL_MIR)) F2(ring_u, sl + 4 * k + 4) = uu[k];
+              if (HAS(k, FL_MIN)) F2(ring_u, sl + 4 * k - 4) = uu[k];
               // energy coefficients of the node (see rk_rate): cl, E1 / (3 div u), E2 / (3 div u)
               const float br = p.eos_b * rho[k];
               const float z = __fdividef(p.akap1_cv3 * rho[k], fmaf(br, 2.0f - br, 1.0f));
@@ -513,7 +524,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
 #pragma unroll
             for (int k = 0; k < CPT; k++)
               F1(ring_T2, sl + 4 * k) =
-                  q < 0 ? twall[k] : (adi_top[k] ? F1(ring_T2, R4(5) + 4 * k) : twall_top[k]);
+                  q < 0 ? TWALL(k) : (HAS(k, FL_ADT) ? F1(ring_T2, R4(5) + 4 * k) : TWALL_TOP(k));
           } else {
             float2 um[CPT + 2], u0[CPT + 2], up[CPT + 2];
             ring_row2<CPT>(ring_u, R4(5), um);
@@ -541,7 +552,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
               const float uxs = uo.x * (1.0f / 3.0f), uys = uo.y * (1.0f / 3.0f);
               const float Tb = t0[k + 1];
               const float h1 = rk_rate<CPT>(p, tm, t0, tp, k, uxs, uys, cf.x, E1, E2);
-              v[k] = col_in[k] ? pg.T_inlet_dev : Tb + 0.5f * h1;
+              v[k] = HAS(k, FL_IN) ? pg.T_inlet_dev : Tb + 0.5f * h1;
               F4(ring_o1, OWN(o, k)) = make_float4(uxs, uys, cf.x, E1);
               F2(ring_o2, OWN(o, k)) = make_float2(E2, Tb);
               F1(ring_acc, OWN(o, k)) = h1;
@@ -549,8 +560,8 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
             ring_put<CPT>(ring_T2, sl, v, allT, wT);
 #pragma unroll
             for (int k = 0; k < CPT; k++) {
-              if (mirror[k]) F1(ring_T2, sl + 4 * k + 4) = v[k];
-              if (adi_bot[k] && q == 0) F1(ring_T2, R4(5) + 4 * k) = v[k];
+              if (HAS(k, FL_MIR)) F1(ring_T2, sl + 4 * k + 4) = v[k];
+              if (HAS(k, FL_ADB) && q == 0) F1(ring_T2, R4(5) + 4 * k) = v[k];
             }
           }
         }
@@ -566,7 +577,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
 #pragma unroll
           for (int k = 0; k < CPT; k++)
             F1(dst, sl + 4 * k) =
-                q < 0 ? twall[k] : (adi_top[k] ? F1(dst, below + 4 * k) : twall_top[k]);
+                q < 0 ? TWALL(k) : (HAS(k, FL_ADT) ? F1(dst, below + 4 * k) : TWALL_TOP(k));
         } else {
           float sm[CPT + 2], s0[CPT + 2], sp[CPT + 2];
           ring_row<CPT>(src, below, sm);
@@ -578,14 +589,14 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
             const float4 w1 = F4(ring_o1, OWN(o, k));
             const float2 w2 = F2(ring_o2, OWN(o, k));
             const float h = rk_rate<CPT>(p, sm, s0, sp, k, w1.x, w1.y, w1.z, w1.w, w2.x);
-            v[k] = col_in[k] ? pg.T_inlet_dev : (full ? w2.y + h : w2.y + 0.5f * h);
+            v[k] = HAS(k, FL_IN) ? pg.T_inlet_dev : (full ? w2.y + h : w2.y + 0.5f * h);
             F1(ring_acc, OWN(o, k)) += 2.0f * h;
           }
           ring_put<CPT>(dst, sl, v, allT, wT);
 #pragma unroll
           for (int k = 0; k < CPT; k++) {
-            if (mirror[k]) F1(dst, sl + 4 * k + 4) = v[k];
-            if (adi_bot[k] && q == 0) F1(dst, below + 4 * k) = v[k];
+            if (HAS(k, FL_MIR)) F1(dst, sl + 4 * k + 4) = v[k];
+            if (HAS(k, FL_ADB) && q == 0) F1(dst, below + 4 * k) = v[k];
           }
         }
       };
@@ -636,7 +647,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
 #pragma unroll
         for (int k = 0; k < CPT; k++) {
           F1(ring_T, sT + 4 * k) =
-              r < 0 ? twall[k] : (adi_top[k] ? F1(ring_T, R8(1) + 4 * k) : twall_top[k]);
+              r < 0 ? TWALL(k) : (HAS(k, FL_ADT) ? F1(ring_T, R8(1) + 4 * k) : TWALL_TOP(k));
           F1(ring_psi, sl + 4 * k) = 0.0f;
         }
       } else {
@@ -649,7 +660,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
           drhoC[k] = drho;
           unsigned st_psi = 0u;
           if (MP) dpsi[k] = pseudopotential_dev(p, drho, Tc[k], st_psi);
-          if (!ghost[k]) {
+          if (!HAS(k, FL_IN | FL_OUT)) {
             st |= st_psi;  // a ghost's populations include unfixed placeholders
             drho_min = fminf(drho_min, drho);
             drho_max = fmaxf(drho_max, drho);
@@ -661,15 +672,15 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
         ring_put<CPT>(ring_psi, sl, dpsi, allS0, wS0);
 #pragma unroll
         for (int k = 0; k < CPT; k++) {
-          if (mirror[k]) {
+          if (HAS(k, FL_MIR)) {
             F1(ring_T, sT + 4 * k + 4) = Tc[k];
             F1(ring_psi, sl + 4 * k + 4) = dpsi[k];
           }
-          if (mirror_in0[k]) {
+          if (HAS(k, FL_MIN0)) {
             F1(ring_T, sT + 4 * k - 4) = pg.T_inlet_dev;
             F1(ring_psi, sl + 4 * k - 4) = dpsi[k];
           }
-          if (adi_bot[k] && r == 0) F1(ring_T, R8(1) + 4 * k) = Tc[k];
+          if (HAS(k, FL_ADB) && r == 0) F1(ring_T, R8(1) + 4 * k) = Tc[k];
         }
       }
     }
@@ -717,6 +728,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
   if (!(p.T_ref + dT_min > 0.0f)) st |= ST_T_NONPOS;
   set_status(status, st);
 #undef OWN
+#undef HAS
+#undef TWALL
+#undef TWALL_TOP
 }
 
 }  // namespace
