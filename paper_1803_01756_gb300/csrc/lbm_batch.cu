@@ -95,14 +95,17 @@ double schedule(const lbm_batch *b, const std::vector<const lbm_lattice *> &orde
 // 512 x 64 (16 rows, 2.8x the 64-row rate), 20 of 1024 x 256, one of 4096 x 512 and 96
 // uneven channels.  When that leaves fewer tiles than SMs, most of the GPU would idle:
 // then heights down to one row compete, each makespan weighted by the time of a row step
-// with k tiles per SM (relative 0.85, 0.97, 1.42, 1.64 for k = 1 .. 4: one CTA alone is
-// bound by the latency of its row step, four share the issue slots), so that a few small
-// lattices spread over the SMs (200 x 50 alone: 1 row, 17.0 against 39.3 us per update
-// with 16; 1024 x 128: 4 rows, 22.8 against 39.6 us).
+// with k tiles per SM (relative, as in the single-lattice tiling: 0.85, 1.0, 1.15 for
+// k = 1 .. 3 with FP32 storage, three CTAs per SM; 0.85, 0.97, 1.42, 1.64 for k = 1 .. 4
+// with 16-bit storage, four: one CTA alone is bound by the latency of its row step, a
+// full SM shares the issue slots), so that a few small lattices spread over the SMs
+// (200 x 50 alone: 1 row, 17.0 against 39.3 us per update with 16; 1024 x 128: 4 rows,
+// 22.8 against 39.6 us).
 int default_rows(const lbm_batch *b) {
   static const int tall[] = {128, 96, 64, 48, 32, 24, 16};
   static const int small[] = {16, 12, 8, 6, 4, 3, 2, 1};
-  static const double kStep[5] = {0.0, 0.85, 0.97, 1.42, 1.64};
+  static const double kStep3[4] = {0.0, 0.85, 1.0, 1.15};
+  static const double kStep4[5] = {0.0, 0.85, 0.97, 1.42, 1.64};
   std::vector<const lbm_lattice *> order(b->lat.begin(), b->lat.end());
   std::stable_sort(order.begin(), order.end(), [](const lbm_lattice *x, const lbm_lattice *y) {
     return (long long)x->nx * x->ny > (long long)y->nx * y->ny;
@@ -121,6 +124,7 @@ int default_rows(const lbm_batch *b) {
   }
   if (best_tiles >= b->sms) return best;
   const int occ = std::max(1, std::min(4, b->grid / b->sms));
+  const double *kStep = occ >= 4 ? kStep4 : kStep3;
   best_cost = 0.0;
   for (int H : small) {
     long long n = 0;

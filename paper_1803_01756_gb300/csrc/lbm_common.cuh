@@ -312,18 +312,41 @@ __device__ __forceinline__ void pull(const DevParams &p, const typename S::T *__
   pull_fix(p, x, sc, g, unknown);
 }
 
+// Two-lane FP32 arithmetic: the packed add, multiply and fused multiply-add of sm_100 and
+// later compute an x and a y term in one instruction.  Each lane rounds as the scalar
+// operation does (round to nearest even; a - b as the fused (-1) b + a, which rounds once,
+// like the subtraction), so a paired expression gives the bits of its scalar form.
+struct P2 {
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
+    return __ffma2_rn(make_float2(-1.0f, -1.0f), b, a);
+  }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, c);
+  }
+};
+
 // rho u = sum e_i g_i + F/2 (Eq. 13; sum e_i w_i rho_ref = 0), summed in one fixed order
 // wherever a velocity is formed, so that a node's velocity has the same bits whichever
 // code path (collision or halo row) computes it
 __device__ __forceinline__ void momentum(const float g[9], float Fx, float Fy, float &jxe,
                                          float &jye) {
-  const float d57 = g[5] - g[7], d68 = g[6] - g[8];
-  jxe = fmaf(0.5f, Fx, (g[1] - g[3]) + (d57 - d68));
-  jye = fmaf(0.5f, Fy, (g[2] - g[4]) + (d57 + d68));
+  // x and y pairwise: (g1 - g3, g2 - g4) + (d57 - d68, d57 + d68), then + F/2
+  const float2 d1324 = P2::sub(make_float2(g[1], g[2]), make_float2(g[3], g[4]));
+  const float2 d5768 = P2::sub(make_float2(g[5], g[6]), make_float2(g[7], g[8]));
+  const float2 dxy = make_float2(d5768.x - d5768.y, d5768.x + d5768.y);
+  const float2 je = P2::fma(make_float2(0.5f, 0.5f), make_float2(Fx, Fy), P2::add(d1324, dxy));
+  jxe = je.x;
+  jye = je.y;
 }
 
+// sum of the nine deviations (density deviation, Eq. 13), opposite directions first and
+// the x and y pairs in one two-lane add each
 __device__ __forceinline__ float sum9(const float g[9]) {
-  return g[0] + (g[1] + g[2] + g[3] + g[4]) + (g[5] + g[6] + g[7] + g[8]);
+  const float2 s1324 = P2::add(make_float2(g[1], g[2]), make_float2(g[3], g[4]));
+  const float2 s5768 = P2::add(make_float2(g[5], g[6]), make_float2(g[7], g[8]));
+  return g[0] + (s1324.x + s1324.y) + (s5768.x + s5768.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -381,22 +404,29 @@ __device__ __forceinline__ void collide(const DevParams &p, const float g[9], fl
                                         float Fy, float fm2, float gs[9], float &rho_out,
                                         float &ux_out, float &uy_out) {
   // n = M g (Eq. 6 on deviations; m = n + rho_ref (1, -2, 1, 0, ...))
-  // sums and differences of opposite directions, shared by the moments
-  const float s13 = g[1] + g[3], s24 = g[2] + g[4], s57 = g[5] + g[7], s68 = g[6] + g[8];
-  const float d13 = g[1] - g[3], d24 = g[2] - g[4], d57 = g[5] - g[7], d68 = g[6] - g[8];
+  // sums and differences of opposite directions, shared by the moments; the x and y
+  // halves of each pair of like terms go through one two-lane instruction (P2 below)
+  const float2 g12 = make_float2(g[1], g[2]), g34 = make_float2(g[3], g[4]);
+  const float2 g56 = make_float2(g[5], g[6]), g78 = make_float2(g[7], g[8]);
+  const float2 s1324 = P2::add(g12, g34), d1324 = P2::sub(g12, g34);
+  const float2 s5768 = P2::add(g56, g78), d5768 = P2::sub(g56, g78);
+  const float s13 = s1324.x, s24 = s1324.y, s57 = s5768.x, s68 = s5768.y;
+  const float d57 = d5768.x, d68 = d5768.y;
   const float sa = s13 + s24, sd = s57 + s68;
-  const float dx = d57 - d68, dy = d57 + d68;  // diagonal parts of j
+  const float2 dxy = make_float2(d57 - d68, d57 + d68);  // diagonal parts of j
   const float n1 = fmaf(2.0f, sd, fmaf(-4.0f, g[0], -sa));
   const float n2 = fmaf(-2.0f, sa, fmaf(4.0f, g[0], sd));
-  const float jx = d13 + dx, jy = d24 + dy;
-  const float n4 = fmaf(-2.0f, d13, dx), n6 = fmaf(-2.0f, d24, dy);
+  const float2 jxy = P2::add(d1324, dxy);
+  const float2 n46 = P2::fma(make_float2(-2.0f, -2.0f), d1324, dxy);
   const float n7 = s13 - s24, n8 = s57 - s68;
 
   const float rho = p.rho_ref + drho;
   const float inv_rho = __fdividef(1.0f, rho);
-  float jxe, jye;  // rho u (Eq. 13)
-  momentum(g, Fx, Fy, jxe, jye);
-  const float ux = jxe * inv_rho, uy = jye * inv_rho;
+  // rho u (Eq. 13): the tree of momentum() pairwise
+  const float2 Fxy = make_float2(Fx, Fy);
+  const float2 je = P2::fma(make_float2(0.5f, 0.5f), Fxy, jxy);
+  const float2 uxy = P2::mul(je, make_float2(inv_rho, inv_rho));
+  const float jxe = je.x, jye = je.y, ux = uxy.x, uy = uxy.y;
   // products are fused explicitly (fmaf) throughout, so that every copy of this code
   // rounds the same way
   const float uu = fmaf(jxe, ux, jye * uy);  // rho |u|^2 (the factor 3 is in k1[2], k2[2])
@@ -426,28 +456,31 @@ __device__ __forceinline__ void collide(const DevParams &p, const float g[9], fl
                                                                fmaf(p.k1[1], drho, p.k1[0] * n1))));
   const float a2 = fmaf(p.k2[4], fm2, fmaf(p.k2[3], uF, fmaf(p.k2[2], uu,
                                                                fmaf(p.k2[1], drho, p.k2[0] * n2))));
-  const float a3 = (jx + Fx) * (1.0f / 6.0f);
-  const float a4 = fmaf(p.kq[2], Fx, fmaf(p.kq[1], jxe, p.kq[0] * n4));
-  const float a5 = (jy + Fy) * (1.0f / 6.0f);
-  const float a6 = fmaf(p.kq[2], Fy, fmaf(p.kq[1], jye, p.kq[0] * n6));
+  const float2 a35 = P2::mul(P2::add(jxy, Fxy), make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+  const float2 a46 = P2::fma(make_float2(p.kq[2], p.kq[2]), Fxy,
+                             P2::fma(make_float2(p.kq[1], p.kq[1]), je,
+                                     P2::mul(make_float2(p.kq[0], p.kq[0]), n46)));
   const float a7 = fmaf(c7c, fmaf(ux, Fx, -(uy * Fy)),
                         fmaf(c7b, fmaf(jxe, ux, -(jye * uy)), c7a * n7));
   const float a8 = fmaf(c8c, fmaf(ux, Fy, uy * Fx), fmaf(c7b, jxe * uy, c7a * n8));
   // f* = M^-1 m* = M^T D^-1 m*
   const float b_ax = a0 - a1 - 2.0f * a2;   // common part of f1..f4
   const float b_dg = a0 + 2.0f * a1 + a2;   // common part of f5..f8
-  const float px = a3 - 2.0f * a4, py = a5 - 2.0f * a6;
-  const float qs = (a3 + a4) + (a5 + a6), qd = (a5 + a6) - (a3 + a4);
-  const float bxp = b_ax + a7, bxm = b_ax - a7, bdp = b_dg + a8, bdm = b_dg - a8;
+  const float2 pxy = P2::fma(make_float2(-2.0f, -2.0f), a46, a35);  // a3 - 2 a4, a5 - 2 a6
+  const float2 t = P2::add(a35, a46);                                // a3 + a4, a5 + a6
+  const float2 q = make_float2(t.x + t.y, t.y - t.x);               // qs, qd
+  const float2 bx = make_float2(b_ax + a7, b_ax - a7), bd = make_float2(b_dg + a8, b_dg - a8);
   gs[0] = a0 - 4.0f * a1 + 4.0f * a2;
-  gs[1] = bxp + px;
-  gs[2] = bxm + py;
-  gs[3] = bxp - px;
-  gs[4] = bxm - py;
-  gs[5] = bdp + qs;
-  gs[6] = bdm + qd;
-  gs[7] = bdp - qs;
-  gs[8] = bdm - qd;
+  const float2 g12o = P2::add(bx, pxy), g34o = P2::sub(bx, pxy);
+  const float2 g56o = P2::add(bd, q), g78o = P2::sub(bd, q);
+  gs[1] = g12o.x;
+  gs[2] = g12o.y;
+  gs[3] = g34o.x;
+  gs[4] = g34o.y;
+  gs[5] = g56o.x;
+  gs[6] = g56o.y;
+  gs[7] = g78o.x;
+  gs[8] = g78o.y;
   rho_out = rho;
   ux_out = ux;
   uy_out = uy;

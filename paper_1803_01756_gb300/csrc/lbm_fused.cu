@@ -18,7 +18,7 @@ namespace {
 
 cudaError_t prepare(const DevParams &p, int storage, int cpt, int *occ) {
   if (cpt == 2) return fused_c2_prepare(p, storage, occ);
-  return prepare_any<FNT, 1, LBM_FUSED_MIN_CTAS>(p, storage, occ);
+  return prepare_any<FNT, 1, FMIN_F32, FMIN_16>(p, storage, occ);
 }
 
 // CTAs across the lattice: at least ceil(nx / W) strips; with CPT = 2 also enough that
@@ -44,14 +44,21 @@ FusedTiling fused_tiling(const DevParams &p, int storage, int device, int cpt) {
   // Widest strips (fewest halo columns), then the row-chunk height H with the shortest
   // estimated launch time over one wave of resident CTAs.  Every CTA sweeps H + 15 row
   // steps, and a row step takes longer the more CTAs share the SM: one CTA alone is bound
-  // by the latency of the row step, four share the SM's issue slots.  kStep is the
-  // measured time of one row step with k CTAs of 128 threads per SM, relative (200 x 50,
-  // 1024 x 128 and 4096 x 512 channels, FP32, one column per thread); equal-work tilings
-  // with narrower strips or two waves were 2-35 % slower on 4096 x 512.  A small lattice
-  // thus gets short chunks spread over idle SMs (1 row on 200 x 50, 2x the rate of 16-row
-  // chunks), a large one one wave of tall chunks.  With two columns per thread a CTA's
-  // row step carries twice the work, so its k CTAs count as 2k.
-  static const double kStep[5] = {0.0, 0.85, 0.97, 1.42, 1.64};
+  // by the latency of the row step, a full SM shares its issue slots.  kStep[k] is the
+  // measured time of one row step with k CTAs of 128 threads per SM, relative, for the
+  // build that fits three per SM (FP32 storage; 4096 x 512: 1.20 us with three, 1.04 us
+  // with two; 1024 x 128 and 200 x 50: one CTA about 0.83 of two) and the one that fits
+  // four (16-bit storage, and two columns per thread, whose k CTAs count as 2k: a CTA's
+  // row step carries twice the work).  Beyond one wave the time grows with k.  Equal-work
+  // tilings with narrower strips or two waves were 2-35 % slower on 4096 x 512.  A small
+  // lattice thus gets short chunks spread over idle SMs (1 row on 200 x 50, 2x the rate of
+  // 16-row chunks), a large one one wave of tall chunks (FP32: 40 rows on 4096 x 512, 683
+  // on 16384 x 2048).
+  static const double kStep3[4] = {0.0, 0.85, 1.0, 1.15};
+  static const double kStep4[5] = {0.0, 0.85, 0.97, 1.42, 1.64};
+  const bool four = occ >= 4 || cpt == 2;
+  const double *kStep = four ? kStep4 : kStep3;
+  const int kmax = four ? 4 : 3;
   const int W = fused_max_width(cpt);
   const long long slots = (long long)sms * occ;
   const int strips = strips_of(p, W, cpt);
@@ -64,7 +71,7 @@ FusedTiling fused_tiling(const DevParams &p, int storage, int device, int cpt) {
     const int h = (int)((p.ny + c - 1) / c);
     const long long tiles = (long long)strips * ((p.ny + h - 1) / h);
     const long long k = ((tiles + sms - 1) / sms) * cpt;  // CTA-equivalents per SM
-    const double step = k <= 4 ? kStep[k] : kStep[4] * (double)k / 4.0;
+    const double step = k <= kmax ? kStep[k] : kStep[kmax] * (double)k / kmax;
     const double cost = (h + 15) * step;
     if (best_cost < 0.0 || cost < best_cost) {  // ties keep the taller chunk
       best_cost = cost;
@@ -83,7 +90,7 @@ cudaError_t launch_fused(const DevParams &p, int storage, const void *gs, void *
   const dim3 grid(strips_of(p, tl.W, tl.cpt), (p.ny + tl.H - 1) / tl.H);
   if (tl.cpt == 2) return fused_c2_launch(p, storage, gs, gout, Tin, Tout, status, sc, grid, s);
   if (tl.cpt != 1) return cudaErrorInvalidValue;
-  return launch_any<FNT, 1, LBM_FUSED_MIN_CTAS>(p, storage, gs, gout, Tin, Tout, status, sc, grid,
+  return launch_any<FNT, 1, FMIN_F32, FMIN_16>(p, storage, gs, gout, Tin, Tout, status, sc, grid,
                                                 s);
 }
 

@@ -68,11 +68,12 @@ cudaError_t prepare_t(const DevParams &p, int *occ) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, NT, smem);
 }
 
-template <int NT, int CPT, int MINB>
+// M32 / M16: resident CTAs per SM the registers are sized for with FP32 / 16-bit storage
+template <int NT, int CPT, int M32, int M16>
 cudaError_t prepare_any(const DevParams &p, int storage, int *occ) {
-  return storage == STORAGE_BF16  ? prepare_t<StoreBF16, NT, CPT, MINB>(p, occ)
-         : storage == STORAGE_F16 ? prepare_t<StoreF16, NT, CPT, MINB>(p, occ)
-                                  : prepare_t<StoreF32, NT, CPT, MINB>(p, occ);
+  return storage == STORAGE_BF16  ? prepare_t<StoreBF16, NT, CPT, M16>(p, occ)
+         : storage == STORAGE_F16 ? prepare_t<StoreF16, NT, CPT, M16>(p, occ)
+                                  : prepare_t<StoreF32, NT, CPT, M32>(p, occ);
 }
 
 template <class ST, int NT, int CPT, int MINB>
@@ -84,17 +85,17 @@ cudaError_t launch_t(const DevParams &p, const void *gs, void *gout, const float
   return cudaGetLastError();
 }
 
-template <int NT, int CPT, int MINB>
+template <int NT, int CPT, int M32, int M16>
 cudaError_t launch_any(const DevParams &p, int storage, const void *gs, void *gout,
                        const float *Tin, float *Tout, unsigned *status, const StepScalars *sc,
                        dim3 grid, cudaStream_t s) {
   switch (storage) {
     case STORAGE_BF16:
-      return launch_t<StoreBF16, NT, CPT, MINB>(p, gs, gout, Tin, Tout, status, sc, grid, s);
+      return launch_t<StoreBF16, NT, CPT, M16>(p, gs, gout, Tin, Tout, status, sc, grid, s);
     case STORAGE_F16:
-      return launch_t<StoreF16, NT, CPT, MINB>(p, gs, gout, Tin, Tout, status, sc, grid, s);
+      return launch_t<StoreF16, NT, CPT, M16>(p, gs, gout, Tin, Tout, status, sc, grid, s);
     default:
-      return launch_t<StoreF32, NT, CPT, MINB>(p, gs, gout, Tin, Tout, status, sc, grid, s);
+      return launch_t<StoreF32, NT, CPT, M32>(p, gs, gout, Tin, Tout, status, sc, grid, s);
   }
 }
 

@@ -29,6 +29,8 @@
 // a node gets the same bits for any tiling and either CPT.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -39,9 +41,13 @@ namespace {
 #define LBM_FUSED_THREADS 128
 #endif
 constexpr int FNT = LBM_FUSED_THREADS;  // threads per CTA of the CPT = 1 kernel
-#ifndef LBM_FUSED_MIN_CTAS
-#define LBM_FUSED_MIN_CTAS (512 / LBM_FUSED_THREADS)
-#endif
+// Resident CTAs per SM that the register budget of the one-column kernels is sized for,
+// by population storage.  With FP32 storage three 128-thread CTAs (168 registers a thread)
+// beat four (128): the six stages of a row step are independent chains, and the extra
+// registers let the compiler overlap them (4096 x 512: 65.9 against 66.5 us per update,
+// 1024 x 128: 15.7 against 16.3 us, the batched kernel 3 % faster).  With 16-bit storage
+// four stay faster (4096 x 512: 71.5 against 76.2 us).
+constexpr int FMIN_F32 = 384 / FNT, FMIN_16 = 512 / FNT;
 
 // left halo columns of a CTA: psi is needed 5 nodes beyond the outputs; with two columns
 // per thread one more keeps the pairs aligned
@@ -57,7 +63,7 @@ struct FusedSmemT {
   float4 pad_lo;         // neighbour reads of the first column below the first ring
   float psi[4][NC];      // psi - psi_r, rows j-3 .. j
   float2 u[4][NC];       // velocity, rows j-5 .. j-2
-  float4 cf[4][NC];      // energy coefficients of rho (cl, E1/(3 div u), E2/(3 div u), -), same rows
+  float4 cf[4][NC];      // energy coefficients of rho (E1/(3 div u), E2/(3 div u), cl, -), same rows
   float T[8][NC];        // T - T_ref, rows j-5 .. j
   float T2[4][NC], T3[4][NC], T4[4][NC];  // RK stage fields
   // own-column values of rows j-10 .. j-4: (ux/3, uy/3, cl, E1), (E2, Tb) and the RK4 sum
@@ -157,12 +163,15 @@ __device__ __forceinline__ float rk_rate(const DevParams &p, const float (&m)[CP
                                          int k, float uxs, float uys, float cl, float E1,
                                          float E2) {
   const float c = z[k + 1];
-  const float v1 = z[k + 2], v3 = z[k], v2 = pp[k + 1], v4 = m[k + 1];
-  const float v5 = pp[k + 2], v6 = pp[k], v7 = m[k], v8 = m[k + 2];
-  const float d57 = v5 - v7, d86 = v8 - v6;
-  const float gx = fmaf(0.25f, d57 + d86, v1 - v3);
-  const float gy = fmaf(0.25f, d57 - d86, v2 - v4);
-  const float lap = fmaf(-5.0f, c, fmaf(0.25f, (v5 + v7) + (v6 + v8), (v1 + v3) + (v2 + v4)));
+  // the x and y terms pairwise: (v1, v2) -+ (v3, v4) and (v5, v8) -+ (v7, v6)
+  const float2 v12 = make_float2(z[k + 2], pp[k + 1]), v34 = make_float2(z[k], m[k + 1]);
+  const float2 v58 = make_float2(pp[k + 2], m[k + 2]), v76 = make_float2(m[k], pp[k]);
+  const float2 d1324 = P2::sub(v12, v34), s1324 = P2::add(v12, v34);
+  const float2 d5786 = P2::sub(v58, v76), s5786 = P2::add(v58, v76);
+  const float d57 = d5786.x, d86 = d5786.y;
+  const float2 g = P2::fma(make_float2(0.25f, 0.25f), make_float2(d57 + d86, d57 - d86), d1324);
+  const float gx = g.x, gy = g.y;
+  const float lap = fmaf(-5.0f, c, fmaf(0.25f, s5786.x + s5786.y, s1324.x + s1324.y));
   const float x = fmaf(c, p.inv_Tc, p.xr);  // T/Tc > 0 on fluid nodes
   const float s = x * rsqrtf(x);
   return fmaf(-E2, s, fmaf(-E1, x, fmaf(cl, lap, -fmaf(uxs, gx, uys * gy))));
@@ -438,13 +447,17 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
               if (!sdn && !sup) {
                 // no wall neighbour: F = -G psi sum w dpsi e  (Eq. 9; sum w e = 0), with
                 // Q = 3 sum w dpsi e and fm2 = |Q|^2 = 9 |q|^2
-                const float d57 = dn[5] - dn[7], d86 = dn[8] - dn[6];
-                const float Qx = fmaf(0.25f, d57 + d86, dn[1] - dn[3]);
-                const float Qy = fmaf(0.25f, d57 - d86, dn[2] - dn[4]);
+                // (x and y terms pairwise, as in rk_rate)
+                const float2 d5786 = P2::sub(make_float2(dn[5], dn[8]), make_float2(dn[7], dn[6]));
+                const float2 d1324 = P2::sub(make_float2(dn[1], dn[2]), make_float2(dn[3], dn[4]));
+                const float d57 = d5786.x, d86 = d5786.y;
+                const float2 Q = P2::fma(make_float2(0.25f, 0.25f),
+                                         make_float2(d57 + d86, d57 - d86), d1324);
                 const float gpsi = fmaf(p.G3, dpc, p.G3r);  // -G psi / 3
-                F[k].Fx = gpsi * Qx;
-                F[k].Fy = gpsi * Qy;
-                F[k].fm2 = fmaf(Qx, Qx, Qy * Qy);
+                const float2 Fq = P2::mul(make_float2(gpsi, gpsi), Q);
+                F[k].Fx = Fq.x;
+                F[k].Fy = Fq.y;
+                F[k].fm2 = fmaf(Q.x, Q.x, Q.y * Q.y);
               } else {
                 unsigned solid_mask = 0u;
                 if (sup) solid_mask |= (1u << 2) | (1u << 5) | (1u << 6);
@@ -485,8 +498,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
             for (int k = 0; k < CPT; k++) {
               float jxe, jye;
               momentum(fB[k], F[k].Fx, F[k].Fy, jxe, jye);
-              ux[k] = jxe * inv_rho[k];
-              uy[k] = jye * inv_rho[k];
+              const float2 u2 = P2::mul(make_float2(jxe, jye), make_float2(inv_rho[k], inv_rho[k]));
+              ux[k] = u2.x;
+              uy[k] = u2.y;
             }
           }
           if (TH) {
@@ -501,12 +515,12 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
             for (int k = 0; k < CPT; k++) {
               if (HAS(k, FL_MIR)) F2(ring_u, sl + 4 * k + 4) = uu[k];
               if (HAS(k, FL_MIN)) F2(ring_u, sl + 4 * k - 4) = uu[k];
-              // energy coefficients of the node (see rk_rate): cl, E1 / (3 div u), E2 / (3 div u)
+              // energy coefficients of the node (see rk_rate): E1 / (3 div u), E2 / (3 div u), cl
               const float br = p.eos_b * rho[k];
               const float z = __fdividef(p.akap1_cv3 * rho[k], fmaf(br, 2.0f - br, 1.0f));
               F4(ring_cf, OWN(sl, k)) =
-                  make_float4(p.lam23_cv * inv_rho[k],
-                              __fdividef(p.RTc_cv3, 1.0f - br) - p.kappa_r * z, z, 0.0f);
+                  make_float4(__fdividef(p.RTc_cv3, 1.0f - br) - p.kappa_r * z, z,
+                              p.lam23_cv * inv_rho[k], 0.0f);
             }
           }
         }
@@ -542,19 +556,19 @@ __device__ __forceinline__ void fused_tile(const DevParams &p, const DevParams &
               const float2 a2 = up[k + 1], a4 = um[k + 1];
               const float2 a5 = up[k + 2], a6 = up[k];
               const float2 a7 = um[k], a8 = um[k + 2];
-              // 3 div u = 9 sum w_i u(x+e_i).e_i (the 1/3 is folded into the cf coefficients)
+              // 3 div u = 9 sum w_i u(x+e_i).e_i (the 1/3 is folded into the cf coefficients);
+              // the diagonal part (u5 - u7) + (u8 - u6) with x and y pairwise
+              const float2 d57 = P2::sub(a5, a7), d86 = P2::sub(a8, a6);
               const float divu3 = ((a1.x - a3.x) + (a2.y - a4.y)) +
-                                  0.25f * ((a5.x + a5.y) - (a6.x - a6.y) - (a7.x + a7.y) +
-                                           (a8.x - a8.y));
-              const float2 uo = u0[k + 1];
+                                  0.25f * ((d57.x + d86.x) + (d57.y - d86.y));
               const float4 cf = F4(ring_cf, OWN(R4(4), k));
-              const float E1 = cf.y * divu3, E2 = cf.z * divu3;
-              const float uxs = uo.x * (1.0f / 3.0f), uys = uo.y * (1.0f / 3.0f);
+              const float2 E = P2::mul(make_float2(cf.x, cf.y), make_float2(divu3, divu3));
+              const float2 us = P2::mul(u0[k + 1], make_float2(1.0f / 3.0f, 1.0f / 3.0f));
               const float Tb = t0[k + 1];
-              const float h1 = rk_rate<CPT>(p, tm, t0, tp, k, uxs, uys, cf.x, E1, E2);
+              const float h1 = rk_rate<CPT>(p, tm, t0, tp, k, us.x, us.y, cf.z, E.x, E.y);
               v[k] = HAS(k, FL_IN) ? pg.T_inlet_dev : Tb + 0.5f * h1;
-              F4(ring_o1, OWN(o, k)) = make_float4(uxs, uys, cf.x, E1);
-              F2(ring_o2, OWN(o, k)) = make_float2(E2, Tb);
+              F4(ring_o1, OWN(o, k)) = make_float4(us.x, us.y, cf.z, E.x);
+              F2(ring_o2, OWN(o, k)) = make_float2(E.y, Tb);
               F1(ring_acc, OWN(o, k)) = h1;
             }
             ring_put<CPT>(ring_T2, sl, v, allT, wT);

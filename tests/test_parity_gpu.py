@@ -329,17 +329,19 @@ def test_runs_on_a_side_stream():
 def test_default_tiling_follows_the_lattice_size():
     """The fused kernel's row-chunk height: short chunks spread a small lattice over
     the SMs (each CTA sweeps its rows plus 15, one row step at a time), a large one gets
-    one wave of tall chunks (152 SMs with 4 resident CTAs each)."""
+    one wave of tall chunks (152 SMs with 3 resident CTAs each with FP32 storage, 4 with
+    16-bit storage)."""
     import torch
     from paper_1803_01756_gb300.lattice import Lattice, KERNEL_FUSED
     if torch.cuda.get_device_properties(0).multi_processor_count != 152:
         pytest.skip("heights stated for 152 SMs")
-    expect = {(200, 50): 1, (1024, 128): 4, (4096, 512): 31, (100, 300): 2}
-    for (nx, ny), rows in expect.items():
-        lat = Lattice(nx, ny, inputs.base_params(), kernel=KERNEL_FUSED)
+    expect = {(200, 50, 0): 1, (1024, 128, 0): 4, (4096, 512, 0): 40, (100, 300, 0): 2,
+              (16384, 2048, 0): 683, (4096, 512, 2): 31, (200, 50, 2): 1}
+    for (nx, ny, storage), rows in expect.items():
+        lat = Lattice(nx, ny, inputs.base_params(), kernel=KERNEL_FUSED, storage=storage)
         info = lat.info()
         lat.close()
-        assert (info["tile_cols"], info["tile_rows"]) == (118, rows), (nx, ny, info)
+        assert (info["tile_cols"], info["tile_rows"]) == (118, rows), (nx, ny, storage, info)
         assert info["cols_per_thread"] == 1
 
 
