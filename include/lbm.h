@@ -116,7 +116,9 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out);
 /* Set the state at the current time from host fields: populations f = f^eq(rho, u = 0)
    (the second-order D2Q9 equilibrium), with the open-boundary rules of the current time
    applied to the boundary columns; T (absolute, may be NULL for uniform T0) as given.
-   rho: [ny][nx] host doubles.  Synchronises the stream. */
+   rho: [ny][nx] host doubles.  Synchronises the stream.  A page-locked host array
+   (cudaHostAlloc, cudaMallocHost or cudaHostRegister memory) is read by the kernels
+   directly over the host link; any other is first copied to a device staging array. */
 int lbm_write_fields(lbm_h h, const double *rho, const double *T, void *stream);
 
 /* Advance nsteps lattice updates (Eqs. 1-18 per update): pull-streaming with bounce-back
@@ -139,7 +141,9 @@ int lbm_set_graph(lbm_h h, int enable);
 
 /* Copy the fields of the current time t to host arrays (any may be NULL): rho = sum f,
    u = (sum e f + F/2) / rho (Eq. 13, force of time t), T absolute.  Synchronises the
-   stream.  Returns LBM_ERR_UNSTABLE if device status bits are set (fields still written). */
+   stream.  Returns LBM_ERR_UNSTABLE if device status bits are set (fields still written).
+   Page-locked host arrays are written by the kernels directly, others through a device
+   staging array and a copy. */
 int lbm_read_fields(lbm_h h, double *rho, double *ux, double *uy, double *T, void *stream);
 
 /* FP64 sums over all nodes of rho (the density of Eq. 13, sum_i f_i) and of rho Cv T

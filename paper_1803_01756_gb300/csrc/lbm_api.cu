@@ -1,6 +1,7 @@
 // Host runtime and C ABI (include/lbm.h).
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -545,13 +546,45 @@ cudaError_t dalloc(lbm_lattice *h, T **ptr, size_t count) {
 // Host fields in: rho (and T) go to the device staging array as they are, and kernels
 // form the populations and the pitched FP32 temperature deviations there; the stream
 // orders the reuse of the staging array.
+// Device address of the host range [p, p + bytes) when all of it lies in one page-locked
+// mapping that the device can address (cudaHostAlloc / cudaMallocHost / cudaHostRegister
+// memory: the same registration at both ends and at the same offset), else nullptr.  The
+// field transfers then read and write such host buffers from their kernels over the
+// host link, with no staging copy; any other pointer (pageable memory) takes the copy path.
+void *mapped_host(const void *p, size_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  const char *lo = static_cast<const char *>(p), *hi = lo + bytes - 1;
+  cudaPointerAttributes a{}, b{};
+  if (cudaPointerGetAttributes(&a, lo) != cudaSuccess ||
+      cudaPointerGetAttributes(&b, hi) != cudaSuccess) {
+    cudaGetLastError();  // clear the error that the failed query recorded
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer ||
+      !b.devicePointer)
+    return nullptr;
+  if (static_cast<const char *>(b.devicePointer) - static_cast<const char *>(a.devicePointer) !=
+      (std::ptrdiff_t)(bytes - 1))
+    return nullptr;
+  return a.devicePointer;
+}
+
 int upload_fields(lbm_lattice *h, const double *rho, const double *T, cudaStream_t s) {
   const size_t n = (size_t)h->nx * h->ny;
-  LBM_CUDA(cudaMemcpyAsync(h->rho0, rho, n * sizeof(double), cudaMemcpyHostToDevice, s));
-  LBM_CUDA(lbm::launch_init(h->dp, h->p.storage, h->rho0, h->g[h->cur], s));
+  // page-locked host fields are read by the kernels directly
+  const double *rho_src = static_cast<const double *>(mapped_host(rho, n * sizeof(double)));
+  if (!rho_src) {
+    LBM_CUDA(cudaMemcpyAsync(h->rho0, rho, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    rho_src = h->rho0;
+  }
+  LBM_CUDA(lbm::launch_init(h->dp, h->p.storage, rho_src, h->g[h->cur], s));
   if (T) {
-    LBM_CUDA(cudaMemcpyAsync(h->rho0, T, n * sizeof(double), cudaMemcpyHostToDevice, s));
-    LBM_CUDA(lbm::launch_pitch_T(h->rho0, h->nx, h->ny, h->pitch, h->T_ref, h->T[h->tcur], s));
+    const double *T_src = static_cast<const double *>(mapped_host(T, n * sizeof(double)));
+    if (!T_src) {
+      LBM_CUDA(cudaMemcpyAsync(h->rho0, T, n * sizeof(double), cudaMemcpyHostToDevice, s));
+      T_src = h->rho0;
+    }
+    LBM_CUDA(lbm::launch_pitch_T(T_src, h->nx, h->ny, h->pitch, h->T_ref, h->T[h->tcur], s));
   } else {
     LBM_CUDA(cudaMemsetAsync(h->T[h->tcur], 0, sizeof(float) * h->plane, s));
   }
@@ -756,11 +789,16 @@ int lbm_read_fields(lbm_h h, double *rho, double *ux, double *uy, double *T, voi
     const float *src;
     double add;
   } outs[4] = {{rho, h->rho, 0.0}, {ux, h->ux, 0.0}, {uy, h->uy, 0.0}, {T, h->T[h->tcur], h->T_ref}};
-  // each field is widened to FP64 in the caller's layout in the device staging array
-  // and copied out; the stream orders the reuse of the array
+  // each field is widened to FP64 in the caller's layout: straight into a page-locked
+  // host buffer, else in the device staging array and copied out (the stream orders the
+  // reuse of the array)
   const size_t n = (size_t)h->nx * h->ny;
   for (auto &o : outs) {
     if (!o.dst) continue;
+    if (double *dst = static_cast<double *>(mapped_host(o.dst, n * sizeof(double)))) {
+      LBM_CUDA(lbm::launch_unpitch(o.src, h->nx, h->ny, h->pitch, o.add, dst, s));
+      continue;
+    }
     LBM_CUDA(lbm::launch_unpitch(o.src, h->nx, h->ny, h->pitch, o.add, h->rho0, s));
     LBM_CUDA(cudaMemcpyAsync(o.dst, h->rho0, n * sizeof(double), cudaMemcpyDeviceToHost, s));
   }

@@ -270,9 +270,18 @@ class Lattice:
     def set_graph(self, enable: bool = True):
         _check(self._lib.lbm_set_graph(self._h, int(bool(enable))), "lbm_set_graph")
 
-    def read_fields(self, stream=None, check: bool = True):
+    def read_fields(self, stream=None, check: bool = True, out=None):
+        """(rho, ux, uy, T) as [ny][nx] FP64 arrays.  out: four C-contiguous FP64 arrays of
+        that shape to fill instead of new ones (page-locked ones are written by the kernels
+        directly, with no staging copy)."""
         shp = (self.ny, self.nx)
-        rho, ux, uy, T = (np.empty(shp) for _ in range(4))
+        if out is None:
+            rho, ux, uy, T = (np.empty(shp) for _ in range(4))
+        else:
+            rho, ux, uy, T = out
+            for a in out:
+                if a.shape != shp or a.dtype != np.float64 or not a.flags.c_contiguous:
+                    raise ValueError(f"out arrays must be C-contiguous float64 of shape {shp}")
         rc = self._lib.lbm_read_fields(self._h, _dptr(rho), _dptr(ux), _dptr(uy), _dptr(T),
                                        _stream_ptr(stream))
         if check:

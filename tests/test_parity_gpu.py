@@ -424,3 +424,53 @@ def test_step_refuses_a_stream_under_capture():
     rho = lat.read_fields()[0]
     assert np.isfinite(rho).all()
     lat.close()
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_page_locked_host_fields_equal_pageable_ones(storage):
+    """Page-locked host arrays are read (lbm_write_fields) and written (lbm_read_fields) by
+    the kernels directly over the host link, other arrays through a device staging array
+    and a copy: both give the same bits, also for page-locked views that start inside
+    their allocation."""
+    import torch
+    from paper_1803_01756_gb300.lattice import Lattice
+    w = inputs.workload("channel_200x50")
+    ny, nx = w["ny"], w["nx"]
+    rho0 = inputs.initial_density(w)
+    # absolute temperature: T0 (in units of Tc) with 1 % seeded noise
+    Tc = oracle.critical_temperature(w["params"])
+    T0 = Tc * w["params"]["T0"] * (1.0 + 0.01 * inputs.uniform01(nx * ny, 9).reshape(ny, nx))
+
+    def pinned_view(offset):
+        # a [ny][nx] float64 view `offset` elements into a page-locked allocation
+        buf = torch.zeros(nx * ny + offset + 3, dtype=torch.float64, pin_memory=True)
+        return buf, buf.numpy()[offset:offset + nx * ny].reshape(ny, nx)
+
+    results = []
+    for pinned in (False, True):
+        lat = Lattice(nx, ny, w["params"], storage=storage)
+        keep = []
+        if pinned:
+            b1, rho_in = pinned_view(5)
+            b2, T_in = pinned_view(0)
+            rho_in[:] = rho0
+            T_in[:] = T0
+            keep += [b1, b2]
+        else:
+            rho_in, T_in = rho0.copy(), T0.copy()
+        lat.write_fields(rho_in, T_in)
+        lat.step(50)
+        if pinned:
+            outs = []
+            for off in (0, 1, 7, 2):
+                b, v = pinned_view(off)
+                keep.append(b)
+                outs.append(v)
+            got = lat.read_fields(out=tuple(outs))
+        else:
+            got = lat.read_fields()
+        results.append([np.array(a) for a in got])
+        lat.close()
+    for a, b in zip(*results):
+        assert np.array_equal(a, b)
+        assert np.isfinite(a).all()
