@@ -78,8 +78,9 @@ using BatchFn = void (*)(const BatchChannel *, int, const StepScalars *, int, in
 // the energy equation and the pseudopotential forces are built (nullptr otherwise)
 template <class ST>
 BatchFn<ST> batch_variant(const DevParams &p, int cpt) {
-#define KB(a, b, c, d) \
-  k_fused_batch<a, b, c, d, ST, FNT, 1, std::is_same<ST, StoreF32>::value ? FMIN_F32 : FMIN_16>
+#define KB(a, b, c, d)                                                                      \
+  k_fused_batch<a, b, c, d, ST, FNT, 1,                                                     \
+                std::is_same<ST, StoreF32>::value && (c) && (d) ? FMIN_F32 : FMIN_16>
   static const BatchFn<ST> table[16] = {
       KB(false, false, false, false), KB(false, false, false, true), KB(false, false, true, false),
       KB(false, false, true, true),   KB(false, true, false, false), KB(false, true, false, true),

@@ -42,9 +42,11 @@ template <class ST>
 using FusedFn = void (*)(DevParams, const typename ST::T *, typename ST::T *, const float *,
                          float *, unsigned *, const StepScalars *);
 
-template <class ST, int NT, int CPT, int MINB>
+// MFULL: resident CTAs per SM the registers are sized for in the variants with the energy
+// equation and the pseudopotential forces (TH and MP); MREST: in the others
+template <class ST, int NT, int CPT, int MFULL, int MREST>
 FusedFn<ST> fused_variant(const DevParams &p) {
-#define KF(a, b, c, d) k_fused_step<a, b, c, d, ST, NT, CPT, MINB>
+#define KF(a, b, c, d) k_fused_step<a, b, c, d, ST, NT, CPT, ((c) && (d) ? MFULL : MREST)>
   static const FusedFn<ST> table[16] = {
       KF(false, false, false, false), KF(false, false, false, true), KF(false, false, true, false),
       KF(false, false, true, true),   KF(false, true, false, false), KF(false, true, false, true),
@@ -59,27 +61,28 @@ FusedFn<ST> fused_variant(const DevParams &p) {
 }
 
 // Sets the kernel's shared-memory attribute and returns its resident CTAs per SM.
-template <class ST, int NT, int CPT, int MINB>
+template <class ST, int NT, int CPT, int MFULL, int MREST>
 cudaError_t prepare_t(const DevParams &p, int *occ) {
-  const FusedFn<ST> fn = fused_variant<ST, NT, CPT, MINB>(p);
+  const FusedFn<ST> fn = fused_variant<ST, NT, CPT, MFULL, MREST>(p);
   const int smem = (int)sizeof(FusedSmemT<NT * CPT>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, NT, smem);
 }
 
-// M32 / M16: resident CTAs per SM the registers are sized for with FP32 / 16-bit storage
+// M32: resident CTAs per SM the registers are sized for in the FP32 variants with the
+// energy equation and the pseudopotential forces; M16: in every other variant
 template <int NT, int CPT, int M32, int M16>
 cudaError_t prepare_any(const DevParams &p, int storage, int *occ) {
-  return storage == STORAGE_BF16  ? prepare_t<StoreBF16, NT, CPT, M16>(p, occ)
-         : storage == STORAGE_F16 ? prepare_t<StoreF16, NT, CPT, M16>(p, occ)
-                                  : prepare_t<StoreF32, NT, CPT, M32>(p, occ);
+  return storage == STORAGE_BF16  ? prepare_t<StoreBF16, NT, CPT, M16, M16>(p, occ)
+         : storage == STORAGE_F16 ? prepare_t<StoreF16, NT, CPT, M16, M16>(p, occ)
+                                  : prepare_t<StoreF32, NT, CPT, M32, M16>(p, occ);
 }
 
-template <class ST, int NT, int CPT, int MINB>
+template <class ST, int NT, int CPT, int MFULL, int MREST>
 cudaError_t launch_t(const DevParams &p, const void *gs, void *gout, const float *Tin, float *Tout,
                      unsigned *status, const StepScalars *sc, dim3 grid, cudaStream_t s) {
-  fused_variant<ST, NT, CPT, MINB>(p)<<<grid, NT, sizeof(FusedSmemT<NT * CPT>), s>>>(
+  fused_variant<ST, NT, CPT, MFULL, MREST>(p)<<<grid, NT, sizeof(FusedSmemT<NT * CPT>), s>>>(
       p, static_cast<const typename ST::T *>(gs), static_cast<typename ST::T *>(gout), Tin, Tout,
       status, sc);
   return cudaGetLastError();
@@ -91,11 +94,11 @@ cudaError_t launch_any(const DevParams &p, int storage, const void *gs, void *go
                        dim3 grid, cudaStream_t s) {
   switch (storage) {
     case STORAGE_BF16:
-      return launch_t<StoreBF16, NT, CPT, M16>(p, gs, gout, Tin, Tout, status, sc, grid, s);
+      return launch_t<StoreBF16, NT, CPT, M16, M16>(p, gs, gout, Tin, Tout, status, sc, grid, s);
     case STORAGE_F16:
-      return launch_t<StoreF16, NT, CPT, M16>(p, gs, gout, Tin, Tout, status, sc, grid, s);
+      return launch_t<StoreF16, NT, CPT, M16, M16>(p, gs, gout, Tin, Tout, status, sc, grid, s);
     default:
-      return launch_t<StoreF32, NT, CPT, M32>(p, gs, gout, Tin, Tout, status, sc, grid, s);
+      return launch_t<StoreF32, NT, CPT, M32, M16>(p, gs, gout, Tin, Tout, status, sc, grid, s);
   }
 }
 

@@ -41,12 +41,15 @@ namespace {
 #define LBM_FUSED_THREADS 128
 #endif
 constexpr int FNT = LBM_FUSED_THREADS;  // threads per CTA of the CPT = 1 kernel
-// Resident CTAs per SM that the register budget of the one-column kernels is sized for,
-// by population storage.  With FP32 storage three 128-thread CTAs (168 registers a thread)
-// beat four (128): the six stages of a row step are independent chains, and the extra
-// registers let the compiler overlap them (4096 x 512: 65.9 against 66.5 us per update,
-// 1024 x 128: 15.7 against 16.3 us, the batched kernel 3 % faster).  With 16-bit storage
-// four stay faster (4096 x 512: 71.5 against 76.2 us).
+// Resident CTAs per SM that the register budget of the one-column kernels is sized for.
+// For the full update (energy equation and pseudopotential forces) with FP32 storage three
+// 128-thread CTAs (168 registers a thread) beat four (128): the six stages of a row step
+// are independent chains, and the extra registers let the compiler overlap them (4096 x 512:
+// 65.9 against 66.5 us per update, 1024 x 128: 15.7 against 16.3 us, the batched kernel
+// 3 % faster).  Every other variant keeps four: with 16-bit storage (4096 x 512: 71.5
+// against 76.2 us; the BF16 job server 27,200 against 24,700 jobs/h) and without the
+// energy equation or the forces (58.0 against 52.9 us, 68.8 against 63.4 us), where the
+// shorter row step needs the fourth CTA's warps to cover its latency.
 constexpr int FMIN_F32 = 384 / FNT, FMIN_16 = 512 / FNT;
 
 // left halo columns of a CTA: psi is needed 5 nodes beyond the outputs; with two columns
