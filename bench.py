@@ -36,6 +36,16 @@ BYTES_PER_CELL_UPDATE = 80
 # f and psi and writes f and u; energy reads T, rho, u and writes T.
 SPLIT_KERNEL_BYTES = {"k_density_psi": 36 + 4 + 8, "k_collide": 36 + 4 + 36 + 8,
                       "k_energy": 4 + 4 + 8 + 4, "k_fused_step": 80}
+# The two-pass path: k_stream_collide reads and writes the populations, reads T and writes
+# rho and u (FP32 populations: 36 + 36 + 4 + 12); k_energy_rk4 reads T, rho and u and
+# writes T.  The update as a whole is still measured against the 80 B of the fused update.
+TWOPASS_RK4_BYTES = 4 + 4 + 8 + 4
+
+
+def twopass_sc_bytes(pop_bytes: int) -> int:
+    """Algorithmic bytes per cell of one k_stream_collide launch with pop_bytes-byte
+    populations."""
+    return 2 * 9 * pop_bytes + 4 + 12
 L2_BYTES = 129e6
 # updates per CUDA-graph chunk of lbm_step on the fused path
 GRAPH_CHUNK = 16
@@ -251,7 +261,8 @@ def our_arm(args, world, rank, local, dist):
     w["params"] = dict(w["params"], **PHYSICS[args.physics])
     nx, ny = w["nx"], w["ny"]
     kernel = {"auto": L.KERNEL_AUTO, "split": L.KERNEL_SPLIT, "fused": L.KERNEL_FUSED,
-              "fused1": L.KERNEL_FUSED_1COL, "fused2": L.KERNEL_FUSED_2COL}[args.kernel]
+              "fused1": L.KERNEL_FUSED_1COL, "fused2": L.KERNEL_FUSED_2COL,
+              "twopass": L.KERNEL_TWOPASS}[args.kernel]
     storage = {"f32": 0, "bf16": 1, "f16": 2}[args.storage]
     # algorithmic bytes per cell-update: populations read and written once, T read and written
     bytes_cell = 2 * 9 * (4 if args.storage == "f32" else 2) + 8
@@ -332,7 +343,14 @@ def our_arm(args, world, rank, local, dist):
     shares = {k: v[0] / total_ms for k, v in per_kernel.items()}
     top_name = max(shares, key=shares.get)
     top_ms, top_n = per_kernel[top_name]
-    per_cell = bytes_cell if top_name == "k_fused_step" else SPLIT_KERNEL_BYTES[top_name]
+    if top_name == "k_fused_step":
+        per_cell = bytes_cell
+    elif top_name == "k_stream_collide":
+        per_cell = twopass_sc_bytes(4 if args.storage == "f32" else 2)
+    elif top_name == "k_energy_rk4":
+        per_cell = TWOPASS_RK4_BYTES
+    else:
+        per_cell = SPLIT_KERNEL_BYTES[top_name]
     traffic = args.traffic
     src_hash = fused_source_hash()
     counters_current = src_hash == FUSED_COUNTERS_SOURCE
@@ -395,7 +413,7 @@ def our_arm(args, world, rank, local, dist):
         dt = max_over_ranks(dt, dist)
         # host rho in per job, plus the boundary scalars (12 B per update) that the
         # fused path copies to the device in chunks of 16 updates
-        sc_bytes = 12 if info["kernel"] == L.KERNEL_FUSED else 0
+        sc_bytes = 12 if info["kernel"] in (L.KERNEL_FUSED, L.KERNEL_TWOPASS) else 0
         e2e = {"value": world * cells * inner * reps / dt / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": 8 * cells / inner + sc_bytes,
                "d2h_bytes_per_step": 4 * 8 * cells / inner,
@@ -415,10 +433,11 @@ def our_arm(args, world, rank, local, dist):
                               f"each ({sum(repeats) / 1e3:.2f} s in all; min "
                               f"{min(repeats) / args.steps * 1e3:.2f}, max "
                               f"{max(repeats) / args.steps * 1e3:.2f} us per update)"),
-                   "kernel": {1: "split", 2: "fused"}[info["kernel"]],
+                   "kernel": {1: "split", 2: "fused", 5: "twopass"}[info["kernel"]],
                    "tile": [info["tile_cols"], info["tile_rows"]],
                    "cols_per_thread": info["cols_per_thread"],
-                   "launch": ("16-update CUDA graphs" if info["kernel"] == L.KERNEL_FUSED
+                   "launch": ("16-update CUDA graphs"
+                              if info["kernel"] in (L.KERNEL_FUSED, L.KERNEL_TWOPASS)
                               else "one launch per kernel"),
                    "untimed_updates_before": args.warmup + GRAPH_CHUNK,
                    "parallelism": f"replicas x{world}",
@@ -646,7 +665,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="channel_4096x512", choices=sorted(inputs.WORKLOADS))
-    ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused", "fused1", "fused2"],
+    ap.add_argument("--kernel", default="auto",
+                    choices=["auto", "split", "fused", "fused1", "fused2", "twopass"],
                     help="fused1 / fused2: the fused kernel with one / two lattice columns per thread")
     ap.add_argument("--physics", default="full", choices=sorted(PHYSICS),
                     help="full update, or without the energy equation / the pseudopotential")

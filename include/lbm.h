@@ -57,6 +57,8 @@ extern "C" {
 #define LBM_KERNEL_FUSED 2   /* one launch per update; the library picks the columns per thread */
 #define LBM_KERNEL_FUSED_1COL 3 /* the fused kernel with one lattice column per thread */
 #define LBM_KERNEL_FUSED_2COL 4 /* the fused kernel with two lattice columns per thread */
+#define LBM_KERNEL_TWOPASS 5 /* two launches per update: streaming and collision (Eqs. 6-15),
+                                then the RK4 energy update (Eqs. 16-18) */
 
 /* Problem parameters, copied by value at lbm_create (the caller keeps ownership). */
 typedef struct lbm_params {
@@ -99,9 +101,9 @@ typedef struct lbm_info {
   double Tc;                  /* critical temperature from Eq. 11 */
   double T_ref, rho_ref;      /* deviation references of the stored T and populations */
   size_t device_bytes;        /* device memory held by the handle */
-  int kernel;                 /* kernel path in use (LBM_KERNEL_SPLIT or _FUSED) */
-  int tile_cols, tile_rows;   /* fused kernel: most output columns and rows of one CTA's tile
-                                 (0 on the split path) */
+  int kernel;                 /* kernel path in use (LBM_KERNEL_SPLIT, _FUSED or _TWOPASS) */
+  int tile_cols, tile_rows;   /* fused kernel (two-pass path: its first pass): most output
+                                 columns and rows of one CTA's tile (0 on the split path) */
   int cols_per_thread;        /* fused kernel: lattice columns each thread sweeps (1 or 2;
                                  0 on the split path) */
 } lbm_info_t;

@@ -2,7 +2,7 @@
 
 Each translation unit compiles to an object in parallel, then nvcc links them
 into paper_1803_01756_gb300/_build/liblbm_gb300.so, a plain C ABI shared object
-(include/lbm.h).  The two fused-kernel units use approximate division and square root
+(include/lbm.h).  The fused-kernel and two-pass units use approximate division and square root
 (about 2 ulp) and flushes denormals to zero (no value of the update comes within
 30 orders of magnitude of the denormal range, so only the special-case code of
 the reciprocal and root instructions goes away): its instruction count bounds its
@@ -24,7 +24,8 @@ LIB = os.path.join(BUILD, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 _FAST = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
-PER_FILE = {"lbm_fused.cu": _FAST, "lbm_fused_c2.cu": _FAST, "lbm_fused_batch.cu": _FAST}
+PER_FILE = {"lbm_fused.cu": _FAST, "lbm_fused_c2.cu": _FAST, "lbm_fused_batch.cu": _FAST,
+            "lbm_twopass.cu": _FAST}
 _lock = threading.Lock()
 
 

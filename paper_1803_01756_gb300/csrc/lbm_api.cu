@@ -30,7 +30,8 @@ struct StateHeader {
 };
 
 using namespace lbm_host;
-const char *kKernelNames[KN_COUNT] = {"k_density_psi", "k_collide", "k_energy", "k_fused_step"};
+const char *kKernelNames[KN_COUNT] = {"k_density_psi", "k_collide", "k_energy", "k_fused_step",
+                                       "k_stream_collide", "k_energy_rk4"};
 
 
 }  // namespace
@@ -76,7 +77,7 @@ int validate(int nx, int ny, const lbm_params_t &p) {
   if (!valid_rate(p.s_e) || !valid_rate(p.s_zeta) || !valid_rate(p.s_q)) return LBM_ERR_ARG;
   if (p.storage != LBM_STORAGE_F32 && p.storage != LBM_STORAGE_BF16 && p.storage != LBM_STORAGE_F16)
     return LBM_ERR_ARG;
-  if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_FUSED_2COL) return LBM_ERR_ARG;
+  if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_TWOPASS) return LBM_ERR_ARG;
   if (p.u_period < 0.0 || std::fabs(p.u_amp) >= 1.0) return LBM_ERR_ARG;
   // adiabatic wall columns (outside a non-empty isothermal window) only with periodic x
   const bool adia = (p.top_iso_x1 > p.top_iso_x0 && (p.top_iso_x0 > 0 || p.top_iso_x1 < nx)) ||
@@ -424,8 +425,28 @@ int split_update(lbm_lattice *h, cudaStream_t s) {
   return LBM_OK;
 }
 
-// the fused launch of the current update, with the scalars of slot k of d_sc
+// the two passes of the current update on the two-pass path, with the scalars of slot k
+// of d_sc: A streams and collides (writing rho and u when the energy equation is on), B
+// advances T
+cudaError_t twopass_a(lbm_lattice *h, int k, cudaStream_t s) {
+  return lbm::launch_stream_collide(h->dp, h->p.storage, h->g[h->cur], h->g[1 - h->cur],
+                                    h->T[h->tcur], h->rho, h->ux, h->uy, h->status, h->d_sc + k,
+                                    h->twopass.Ha, s);
+}
+
+cudaError_t twopass_b(lbm_lattice *h, int k, cudaStream_t s) {
+  return lbm::launch_energy_rk4(h->dp, h->T[h->tcur], h->T[1 - h->tcur], h->rho, h->ux, h->uy,
+                                h->status, h->d_sc + k, h->twopass.Hb, s);
+}
+
+// the launches of the current update on the fused or the two-pass path, with the scalars
+// of slot k of d_sc
 cudaError_t fused_launch(lbm_lattice *h, int k, cudaStream_t s) {
+  if (h->kernel == LBM_KERNEL_TWOPASS) {
+    cudaError_t e = twopass_a(h, k, s);
+    if (e == cudaSuccess && h->dp.thermal) e = twopass_b(h, k, s);
+    return e;
+  }
   return lbm::launch_fused(h->dp, h->p.storage, h->g[h->cur], h->g[1 - h->cur], h->T[h->tcur],
                            h->T[1 - h->tcur], h->status, h->d_sc + k, h->fused, s);
 }
@@ -480,8 +501,8 @@ int capture_chunk(lbm_lattice *h) {
   return LBM_OK;
 }
 
-// nsteps fused updates: chunks of kChunk, each a graph replay when graphs are on and
-// per-launch timing is off, else one launch per update
+// nsteps updates on the fused or two-pass path: chunks of kChunk, each a graph replay when
+// graphs are on and per-launch timing is off, else the launches of one update at a time
 int fused_steps(lbm_lattice *h, long nsteps, cudaStream_t s) {
   const int C = lbm_lattice::kChunk;
   for (long done = 0; done < nsteps;) {
@@ -497,7 +518,13 @@ int fused_steps(lbm_lattice *h, long nsteps, cudaStream_t s) {
       h->t += C;  // an even chunk ends at the parity it started from
     } else {
       for (int k = 0; k < m; k++) {
-        rc = timed(h, KN_FUSED, s, [&] { return fused_launch(h, k, s); });
+        if (h->kernel == LBM_KERNEL_TWOPASS) {
+          rc = timed(h, KN_STREAM_COLLIDE, s, [&] { return twopass_a(h, k, s); });
+          if (!rc && h->dp.thermal)
+            rc = timed(h, KN_ENERGY_RK4, s, [&] { return twopass_b(h, k, s); });
+        } else {
+          rc = timed(h, KN_FUSED, s, [&] { return fused_launch(h, k, s); });
+        }
         if (rc) return rc;
         advance(h);
       }
@@ -644,7 +671,22 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
   if (p->x_bc == LBM_X_PRESSURE_INLET)
     h->rho_branch_end = vapour_branch_end(*p, h->Tc, h->Tc * p->T_inlet);
   h->kernel = LBM_KERNEL_SPLIT;
-  if (p->kernel != LBM_KERNEL_SPLIT) {
+  if (p->kernel == LBM_KERNEL_TWOPASS) {
+    // 32-bit element offsets, as on the fused path
+    if (lbm::fused_supported(h->dp)) h->twopass = lbm::twopass_tiling(h->dp, p->storage, h->device);
+    // LBM_TWOPASS_TILE="Ha,Hb" overrides the row-chunk heights (tuning experiments)
+    if (const char *env = std::getenv("LBM_TWOPASS_TILE")) {
+      int Ha = 0, Hb = 0;
+      if (std::sscanf(env, "%d,%d", &Ha, &Hb) == 2 && Ha >= 1 && Hb >= 1 &&
+          (ny + Ha - 1) / Ha <= 65535 && (ny + Hb - 1) / Hb <= 65535 && h->twopass.Ha > 0)
+        h->twopass = lbm::TwoPassTiling{Ha, Hb};
+    }
+    if (h->twopass.Ha < 1) {
+      delete h;
+      return LBM_ERR_ARG;
+    }
+    h->kernel = LBM_KERNEL_TWOPASS;
+  } else if (p->kernel != LBM_KERNEL_SPLIT) {
     // lattice columns per thread of the fused kernel: as asked, else the library's
     // default, which LBM_FUSED_CPT=1|2 overrides (tuning experiments)
     int cpt = default_cpt(nx, ny);
@@ -689,7 +731,7 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
   if (e == cudaSuccess) e = dalloc(h, &h->sums, 2);
   if (e == cudaSuccess) e = dalloc(h, &h->rho0, (size_t)nx * ny);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_sums, 2 * sizeof(double));
-  if (h->kernel == LBM_KERNEL_FUSED) {
+  if (h->kernel == LBM_KERNEL_FUSED || h->kernel == LBM_KERNEL_TWOPASS) {
     const int C = lbm_lattice::kChunk;
     if (e == cudaSuccess) e = dalloc(h, &h->d_sc, C);
     for (int k = 0; k < 2 && e == cudaSuccess; k++)
@@ -742,7 +784,8 @@ int lbm_step(lbm_h h, long nsteps, void *stream) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   LBM_CUDA(cudaStreamIsCapturing(s, &cs));
   if (cs != cudaStreamCaptureStatusNone) return LBM_ERR_ARG;
-  if (h->kernel == LBM_KERNEL_FUSED) return fused_steps(h, nsteps, s);
+  if (h->kernel == LBM_KERNEL_FUSED || h->kernel == LBM_KERNEL_TWOPASS)
+    return fused_steps(h, nsteps, s);
   for (long k = 0; k < nsteps; k++) {
     int rc = split_update(h, s);
     if (rc) return rc;
@@ -886,9 +929,10 @@ int lbm_info(lbm_h h, lbm_info_t *info) {
   info->device_bytes = h->device_bytes;
   info->kernel = h->kernel;
   const bool fused = h->kernel == LBM_KERNEL_FUSED;
-  info->tile_cols = fused ? h->fused.W : 0;
-  info->tile_rows = fused ? h->fused.H : 0;
-  info->cols_per_thread = fused ? h->fused.cpt : 0;
+  const bool two = h->kernel == LBM_KERNEL_TWOPASS;
+  info->tile_cols = fused ? h->fused.W : two ? lbm::twopass_width_a() : 0;
+  info->tile_rows = fused ? h->fused.H : two ? h->twopass.Ha : 0;
+  info->cols_per_thread = fused ? h->fused.cpt : two ? 1 : 0;
   return LBM_OK;
 }
 

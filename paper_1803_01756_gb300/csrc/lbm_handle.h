@@ -9,7 +9,7 @@
 
 namespace lbm_host {
 
-enum { KN_DENSITY = 0, KN_COLLIDE, KN_ENERGY, KN_FUSED, KN_COUNT };
+enum { KN_DENSITY = 0, KN_COLLIDE, KN_ENERGY, KN_FUSED, KN_STREAM_COLLIDE, KN_ENERGY_RK4, KN_COUNT };
 
 struct TimedLaunch {
   int kind;
@@ -29,6 +29,7 @@ struct lbm_lattice {
   long long t = 0;
   int kernel = LBM_KERNEL_SPLIT;
   lbm::FusedTiling fused{0, 0, 1};  // CTA tiling of the fused kernel
+  lbm::TwoPassTiling twopass{0, 0};  // row-chunk heights of the two-pass path
   int cur = 0;   // g[cur]: post-collision populations of the previous update
   int tcur = 0;  // T[tcur]: temperature deviation of time t
   void *g[2] = {nullptr, nullptr};  // populations, storage-typed elements
@@ -59,8 +60,8 @@ struct lbm_lattice {
   bool timing = false;
   std::vector<lbm_host::TimedLaunch> pending;
   std::vector<cudaEvent_t> pool;
-  double total_ms[lbm_host::KN_COUNT] = {0, 0, 0, 0};
-  long launches[lbm_host::KN_COUNT] = {0, 0, 0, 0};
+  double total_ms[lbm_host::KN_COUNT] = {};
+  long launches[lbm_host::KN_COUNT] = {};
 };
 
 

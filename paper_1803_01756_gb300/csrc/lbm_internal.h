@@ -70,6 +70,25 @@ int fused_batch_grid(const DevParams &mode, int storage, int cpt, int device);
 // output columns of one CTA of the batched kernel with cpt columns per thread
 int fused_batch_width(int cpt);
 
+// two-pass path (lbm_twopass.cu): pass A streams and collides (and, with the energy
+// equation on, writes rho and u of every node), pass B advances T with the RK4 stages;
+// Ha and Hb are the row-chunk heights of the two launches
+struct TwoPassTiling {
+  int Ha, Hb;
+};
+// chunk heights for this device ({0, 0} on failure); also sets pass B's shared-memory
+// attribute
+TwoPassTiling twopass_tiling(const DevParams &p, int storage, int device);
+int twopass_width_a();  // output columns of a pass-A CTA
+int twopass_width_b();  // output columns of a pass-B CTA
+cudaError_t launch_stream_collide(const DevParams &p, int storage, const void *gs, void *gout,
+                                  const float *Tin, float *rho, float *ux, float *uy,
+                                  unsigned *status, const StepScalars *sc, int Ha,
+                                  cudaStream_t s);
+cudaError_t launch_energy_rk4(const DevParams &p, const float *Tin, float *Tout, const float *rho,
+                              const float *ux, const float *uy, unsigned *status,
+                              const StepScalars *sc, int Hb, cudaStream_t s);
+
 // set-up and reductions
 cudaError_t launch_init(const DevParams &p, int storage, const double *rho0, void *gout,
                         cudaStream_t s);

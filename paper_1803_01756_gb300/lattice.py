@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm_gb300.so")
 LBM_OK = 0
 ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_UNSTABLE",
           -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_BUSY", -7: "LBM_ERR_STATE"}
-KERNEL_AUTO, KERNEL_SPLIT, KERNEL_FUSED, KERNEL_FUSED_1COL, KERNEL_FUSED_2COL = 0, 1, 2, 3, 4
+KERNEL_AUTO, KERNEL_SPLIT, KERNEL_FUSED, KERNEL_FUSED_1COL, KERNEL_FUSED_2COL, KERNEL_TWOPASS = (
+    0, 1, 2, 3, 4, 5)
 STORAGE_F32 = 0
 
 

@@ -7,8 +7,8 @@ the velocity vector u (|.| is the Euclidean norm per node) and T.  The velocity
 scale is floored at U_FLOOR = 1e-3, so that nearly quiescent lattices (|u| down to
 1e-7) are compared in absolute terms (1e-8 in lattice units) instead of relative to
 their own noise, and at the acoustic image of the measured density error (see
-rel_errors).  Each case runs on the three GPU paths: the split kernels and the fused
-kernel with one and with two lattice columns per thread.
+rel_errors).  Each case runs on the four GPU paths: the split kernels, the fused
+kernel with one and with two lattice columns per thread, and the two-pass path.
 """
 import numpy as np
 import pytest
@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 U_FLOOR = 1e-3
 CS = 3 ** -0.5  # lattice sound speed
-KERNELS = ["split", "fused", "fused2"]
+KERNELS = ["split", "fused", "fused2", "twopass"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,10 +36,10 @@ def _cuda():
 
 def kernel_id(name):
     """split: three launches per update; fused / fused2: the fused kernel with one / two
-    lattice columns per thread."""
+    lattice columns per thread; twopass: streaming and collision, then the energy update."""
     from paper_1803_01756_gb300 import lattice
     return {"split": lattice.KERNEL_SPLIT, "fused": lattice.KERNEL_FUSED_1COL,
-            "fused2": lattice.KERNEL_FUSED_2COL}[name]
+            "fused2": lattice.KERNEL_FUSED_2COL, "twopass": lattice.KERNEL_TWOPASS}[name]
 
 
 def make_lattice(nx, ny, p, kernel):
@@ -47,7 +47,7 @@ def make_lattice(nx, ny, p, kernel):
     try:
         return Lattice(nx, ny, p, kernel=kernel_id(kernel))
     except LbmError as e:
-        if kernel.startswith("fused") and e.code == -1:
+        if kernel != "split" and e.code == -1:
             pytest.skip("fused kernel does not cover this configuration")
         raise
 
@@ -218,7 +218,7 @@ def test_full_size_long_run_properties(kernel):
 
 
 def test_beyond_l2_channel_16384x2048():
-    """16384 x 2048 (2.4 GB of FP32 populations): the fused and the split kernels, each
+    """16384 x 2048 (2.4 GB of FP32 populations): the fused, two-pass and split paths, each
     held to the oracle at the sizes above, agree after 20 updates, with no status bits and
     the FP64 mass reduction equal to the sum of the density field.  (The oracle would take
     about 15 s and 8 GB of host memory per update at this size.)"""
@@ -233,8 +233,9 @@ def test_beyond_l2_channel_16384x2048():
         assert lat.status() == 0
         lat.close()
         assert mass == pytest.approx(out[kernel][0].sum(), rel=1e-12)
-    err = rel_errors(out["fused"], out["split"])
-    assert max(err.values()) <= TOL, err
+    for kernel in KERNELS[1:]:
+        err = rel_errors(out[kernel], out["split"])
+        assert max(err.values()) <= TOL, (kernel, err)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -374,7 +375,7 @@ def test_results_do_not_depend_on_the_tiling(kernel, tile, monkeypatch):
         assert np.array_equal(a, b), (t_ref, t_got)
 
 
-@pytest.mark.parametrize("kernel", ["fused", "fused2"])
+@pytest.mark.parametrize("kernel", ["fused", "fused2", "twopass"])
 @pytest.mark.parametrize("over", [dict(), dict(thermal=0), dict(x_bc=2, p_amp_frac=0.1,
                                                                 u_period=60.0)])
 def test_graph_replay_equals_one_launch_per_update(over, kernel):
@@ -402,6 +403,31 @@ def test_graph_replay_equals_one_launch_per_update(over, kernel):
         lat.close()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tile", ["1,1", "3,5", "17,2", "50,50", "7,16"])
+def test_twopass_results_do_not_depend_on_the_tiling(tile, monkeypatch):
+    """The two passes recompute their halo nodes (a psi row and column for the first, four
+    rows and columns of the energy-equation stages for the second) with the same
+    instructions as the CTA that owns them, so any row-chunk heights give the same bits."""
+    from paper_1803_01756_gb300.lattice import Lattice
+    w = inputs.workload("channel_200x50")
+    rho0 = inputs.initial_density(w)
+
+    def run():
+        lat = Lattice(w["nx"], w["ny"], w["params"], kernel=kernel_id("twopass"))
+        lat.write_fields(rho0)
+        lat.step(200)
+        out, info = lat.read_fields(), lat.info()
+        lat.close()
+        return out, info
+
+    ref, _ = run()
+    monkeypatch.setenv("LBM_TWOPASS_TILE", tile)
+    got, info = run()
+    assert info["tile_rows"] == int(tile.split(",")[0])
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b), tile
 
 
 def test_step_refuses_a_stream_under_capture():
