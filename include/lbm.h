@@ -52,7 +52,8 @@ extern "C" {
 #define LBM_STORAGE_BF16 1   /* stored as BF16 f_i / w_i - rho_ref (FP32 arithmetic) */
 #define LBM_STORAGE_F16 2    /* stored as FP16 f_i / w_i - rho_ref (FP32 arithmetic) */
 
-#define LBM_KERNEL_AUTO 0
+#define LBM_KERNEL_AUTO 0    /* the library's choice: with the energy equation on, the two-pass
+                                path for lattices of at most 2^18 nodes, else the fused kernel */
 #define LBM_KERNEL_SPLIT 1   /* density/psi, collide, energy: three launches per update */
 #define LBM_KERNEL_FUSED 2   /* one launch per update; the library picks the columns per thread */
 #define LBM_KERNEL_FUSED_1COL 3 /* the fused kernel with one lattice column per thread */

@@ -671,6 +671,17 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
   if (p->x_bc == LBM_X_PRESSURE_INLET)
     h->rho_branch_end = vapour_branch_end(*p, h->Tc, h->Tc * p->T_inlet);
   h->kernel = LBM_KERNEL_SPLIT;
+  // The library's choice for the energy equation on lattices of at most 2^18 nodes is the
+  // two-pass path: its halos are one row (collision) and four rows (energy update) where
+  // the fused kernel's short row chunks on a small lattice spend most row steps filling
+  // its six-stage pipeline (GB300: 200 x 50 9.6 against 11.1 us per update, 1024 x 256
+  // 18.9 against 19.7 us; from 2048 x 256 on the fused kernel is faster).
+  const bool auto_two = p->kernel == LBM_KERNEL_AUTO && p->thermal &&
+                        (long long)nx * ny <= (1LL << 18) && lbm::fused_supported(h->dp);
+  if (auto_two) {
+    h->twopass = lbm::twopass_tiling(h->dp, p->storage, h->device);
+    if (h->twopass.Ha > 0) h->kernel = LBM_KERNEL_TWOPASS;
+  }
   if (p->kernel == LBM_KERNEL_TWOPASS) {
     // 32-bit element offsets, as on the fused path
     if (lbm::fused_supported(h->dp)) h->twopass = lbm::twopass_tiling(h->dp, p->storage, h->device);
@@ -686,7 +697,7 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
       return LBM_ERR_ARG;
     }
     h->kernel = LBM_KERNEL_TWOPASS;
-  } else if (p->kernel != LBM_KERNEL_SPLIT) {
+  } else if (p->kernel != LBM_KERNEL_SPLIT && h->kernel != LBM_KERNEL_TWOPASS) {
     // lattice columns per thread of the fused kernel: as asked, else the library's
     // default, which LBM_FUSED_CPT=1|2 overrides (tuning experiments)
     int cpt = default_cpt(nx, ny);

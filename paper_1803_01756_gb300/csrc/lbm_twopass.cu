@@ -144,10 +144,10 @@ __device__ __forceinline__ void pull_index(const DevParams &p, int x, int y, int
 
 // Pass A on one tile: output columns [X0, X0 + W), rows [Y0, ye).  Thread t owns column
 // X0 - 1 + t.  Per row step j (row r = Y0 - 1 + j):
-//   - the populations of row r + 1 are loaded into registers (prefetch, consumed in the
-//     next step, so their latency overlaps a whole step of arithmetic);
-//   - S0 finishes row r (loaded in the previous step): Zou-He fix-up, density, psi into
-//     the ring;  __syncthreads;
+//   - the loads of row r + AND are issued into the staging slots (cp.async), so that a
+//     row's loads have AND row steps of arithmetic to land in;
+//   - S0 finishes row r (staged AND steps ago): Zou-He fix-up, density, psi into the
+//     ring;  __syncthreads;
 //   - S1 collides row r - 1 with the psi of rows r - 2 .. r and stores it.
 // One barrier per step orders S0's ring write before S1's reads of the same step; the
 // next step's write goes to the slot of row r + 1, which no read of this step touches.
