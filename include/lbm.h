@@ -228,7 +228,8 @@ int lbm_droplet_stats(const double *rho, int nx, int ny, double threshold, doubl
 
 /* ---- batched updates of many lattices (one persistent launch per step) ----
    A batch groups lattices that share the boundary modes (x_bc class, y_bc), the
-   thermal and multiphase switches and the storage, and that use the fused kernel;
+   thermal and multiphase switches and the storage, and that use the fused kernel or
+   the two-pass path (LBM_KERNEL_AUTO gives one of the two);
    sizes and all other parameters may differ.  Each step is one launch whose
    resident CTAs take tiles of all lattices from one work-list (largest lattices
    first) through an atomic counter.  The batch borrows the lattices: they stay
@@ -237,8 +238,8 @@ int lbm_droplet_stats(const double *rho, int nx, int ny, double threshold, doubl
    A lattice's fields after lbm_batch_step equal those after lbm_step alone. */
 typedef struct lbm_batch *lbm_batch_h;
 
-/* LBM_ERR_ARG if a lattice is NULL, repeated, on another device, not on the fused
-   kernel, or differs in modes or storage from the first. */
+/* LBM_ERR_ARG if a lattice is NULL, repeated, on another device, on the split path, or
+   differs in modes or storage from the first. */
 int lbm_batch_create(lbm_h *lattices, int n, lbm_batch_h *out);
 /* Advance every lattice of the batch by nsteps updates (enqueued on the stream).
    LBM_ERR_ARG if the stream is being captured into a CUDA graph, as for lbm_step. */

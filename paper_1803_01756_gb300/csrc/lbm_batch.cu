@@ -217,7 +217,11 @@ int lbm_batch_create(lbm_h *lattices, int n, lbm_batch_h *out) {
   if (!first) return LBM_ERR_ARG;
   for (int i = 0; i < n; i++) {
     lbm_lattice *h = lattices[i];
-    if (!h || h->device != first->device || h->kernel != LBM_KERNEL_FUSED) return LBM_ERR_ARG;
+    // lattices on the fused or the two-pass path (both keep the fused kernel's 32-bit
+    // element offsets, which the batched kernel uses)
+    if (!h || h->device != first->device ||
+        (h->kernel != LBM_KERNEL_FUSED && h->kernel != LBM_KERNEL_TWOPASS))
+      return LBM_ERR_ARG;
     if (h->dp.y_walls != first->dp.y_walls || h->dp.x_open != first->dp.x_open ||
         h->dp.thermal != first->dp.thermal || h->dp.multiphase != first->dp.multiphase ||
         h->p.storage != first->p.storage)

@@ -84,6 +84,39 @@ def test_batch_equals_alone(graph, tile_rows, tiling):
         lat.close()
 
 
+def test_batch_takes_lattices_of_the_default_kernel_choice():
+    """Small lattices created with the library's kernel choice run on the two-pass path;
+    a batch takes them like fused-path lattices, and their fields equal the fields of the
+    same lattices stepped alone (two-pass) within the FP32 parity tolerance."""
+    from paper_1803_01756_gb300.lattice import Batch, Lattice, KERNEL_TWOPASS
+    specs = channel_set(4, seed=50)
+    steps = 21
+    alone = []
+    for nx, ny, p, rho0 in specs:
+        lat = Lattice(nx, ny, p)
+        assert lat.info()["kernel"] == KERNEL_TWOPASS
+        lat.write_fields(rho0)
+        lat.step(steps)
+        alone.append(lat.read_fields())
+        lat.close()
+    lats = []
+    for nx, ny, p, rho0 in specs:
+        lat = Lattice(nx, ny, p)
+        lat.write_fields(rho0)
+        lats.append(lat)
+    b = Batch(lats)
+    b.step(steps)
+    for lat, ref in zip(lats, alone):
+        rho, ux, uy, T = lat.read_fields()
+        rr, rux, ruy, rT = ref
+        assert np.abs(rho - rr).max() <= 1e-5 * np.abs(rr).max()
+        assert np.hypot(ux - rux, uy - ruy).max() <= 1e-5 * max(np.hypot(rux, ruy).max(), 1e-3)
+        assert np.abs(T - rT).max() <= 1e-5 * np.abs(rT).max()
+    b.close()
+    for lat in lats:
+        lat.close()
+
+
 def test_batch_rejects_mixed_modes():
     from paper_1803_01756_gb300.lattice import Batch, Lattice, LbmError
     a = Lattice(40, 10, inputs.base_params(), kernel=2)
