@@ -358,7 +358,7 @@ def our_arm(args, world, rank, local, dist):
     counters_current = src_hash == FUSED_COUNTERS_SOURCE
     if (traffic is None and top_name == "k_fused_step" and args.storage == "f32"
             and args.workload == "channel_4096x512" and args.physics == "full"
-            and counters_current):
+            and info["cols_per_thread"] == 1 and counters_current):
         traffic = FUSED_F32_4096x512_DRAM_BYTES
     bytes_per_launch = per_cell * cells
     avg_us = elapsed_ms * shares[top_name] / top_n * 1e3
