@@ -714,7 +714,7 @@ int lbm_create(int nx, int ny, const lbm_params_t *p, lbm_h *out) {
       int W = 0, H = 0;
       if (std::sscanf(env, "%d,%d", &W, &H) == 2 && W >= 1 && W <= lbm::fused_max_width(cpt) &&
           H >= 1 && (ny + H - 1) / H <= 65535 && lbm::fused_supported(h->dp))
-        h->fused = lbm::FusedTiling{W, H, cpt};
+        h->fused = lbm::FusedTiling{W, H, cpt, 0};
     }
     if (h->fused.W > 0) {
       h->kernel = LBM_KERNEL_FUSED;

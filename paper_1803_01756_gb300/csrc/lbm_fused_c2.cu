@@ -22,7 +22,8 @@ cudaError_t fused_c2_prepare(const DevParams &p, int storage, int *occ) {
 cudaError_t fused_c2_launch(const DevParams &p, int storage, const void *gs, void *gout,
                             const float *Tin, float *Tout, unsigned *status, const StepScalars *sc,
                             dim3 grid, cudaStream_t s) {
-  return launch_any<C2T, 2, C2B, C2B>(p, storage, gs, gout, Tin, Tout, status, sc, grid, s);
+  return launch_any<C2T, 2, C2B, C2B>(p, storage, gs, gout, Tin, Tout, status, sc, grid, false,
+                                      s);
 }
 
 }  // namespace lbm

@@ -32,7 +32,14 @@ __global__ void __launch_bounds__(NT, MINB)
   const int ye = (int)(((long long)(blockIdx.y + 1) * p.ny) / gridDim.y);
   // the update's boundary scalars, read where used
   __shared__ StepScalars ssc;
+  // Launched as a programmatic dependent of the previous update (see launch_t), the CTAs
+  // of this update start while the previous grid drains: they allow the next update's
+  // launch at once and read their boundary scalars (staged before the chunk), then wait
+  // for the previous grid to complete and its writes to be visible before touching the
+  // populations and temperatures it wrote or read.  Launched otherwise, both are no-ops.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (threadIdx.x == 0) ssc = *sc;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
   fused_tile<YW, XO, TH, MP, ST, (CPT == 1 ? 2 : 1), NT, CPT>(p, p, gs, gout, Tin, Tout, status,
                                                              ssc, X0, X1 - X0, Y0, ye, S);
@@ -79,26 +86,41 @@ cudaError_t prepare_any(const DevParams &p, int storage, int *occ) {
                                   : prepare_t<StoreF32, NT, CPT, M32, M16>(p, occ);
 }
 
+// pdl: the launch may begin before the previous kernel on the stream completes (programmatic
+// stream serialization; the kernel waits for it before touching the lattice state)
 template <class ST, int NT, int CPT, int MFULL, int MREST>
 cudaError_t launch_t(const DevParams &p, const void *gs, void *gout, const float *Tin, float *Tout,
-                     unsigned *status, const StepScalars *sc, dim3 grid, cudaStream_t s) {
-  fused_variant<ST, NT, CPT, MFULL, MREST>(p)<<<grid, NT, sizeof(FusedSmemT<NT * CPT>), s>>>(
-      p, static_cast<const typename ST::T *>(gs), static_cast<typename ST::T *>(gout), Tin, Tout,
-      status, sc);
-  return cudaGetLastError();
+                     unsigned *status, const StepScalars *sc, dim3 grid, bool pdl,
+                     cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = sizeof(FusedSmemT<NT * CPT>);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, fused_variant<ST, NT, CPT, MFULL, MREST>(p), p,
+                            static_cast<const typename ST::T *>(gs),
+                            static_cast<typename ST::T *>(gout), Tin, Tout, status, sc);
 }
 
 template <int NT, int CPT, int M32, int M16>
 cudaError_t launch_any(const DevParams &p, int storage, const void *gs, void *gout,
                        const float *Tin, float *Tout, unsigned *status, const StepScalars *sc,
-                       dim3 grid, cudaStream_t s) {
+                       dim3 grid, bool pdl, cudaStream_t s) {
   switch (storage) {
     case STORAGE_BF16:
-      return launch_t<StoreBF16, NT, CPT, M16, M16>(p, gs, gout, Tin, Tout, status, sc, grid, s);
+      return launch_t<StoreBF16, NT, CPT, M16, M16>(p, gs, gout, Tin, Tout, status, sc, grid, pdl,
+                                                     s);
     case STORAGE_F16:
-      return launch_t<StoreF16, NT, CPT, M16, M16>(p, gs, gout, Tin, Tout, status, sc, grid, s);
+      return launch_t<StoreF16, NT, CPT, M16, M16>(p, gs, gout, Tin, Tout, status, sc, grid, pdl,
+                                                    s);
     default:
-      return launch_t<StoreF32, NT, CPT, M32, M16>(p, gs, gout, Tin, Tout, status, sc, grid, s);
+      return launch_t<StoreF32, NT, CPT, M32, M16>(p, gs, gout, Tin, Tout, status, sc, grid, pdl,
+                                                    s);
   }
 }
 

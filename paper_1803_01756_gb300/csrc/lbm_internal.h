@@ -39,6 +39,7 @@ struct FusedTiling {
   int W;    // output columns per CTA (at most fused_max_width(cpt))
   int H;    // output rows per CTA
   int cpt;  // lattice columns per thread: 1 or 2
+  int pdl;  // launch each update as a programmatic dependent of the previous one
 };
 cudaError_t launch_fused(const DevParams &p, int storage, const void *gs, void *gout,
                          const float *Tin, float *Tout, unsigned *status, const StepScalars *sc,
