@@ -434,7 +434,9 @@ def test_dependent_launch_gives_the_same_bits(monkeypatch):
     """On 4096 x 512 the fused updates are launched as programmatic dependents of the
     previous update (their CTAs start while it drains and wait for it before touching the
     lattice state); an explicit tiling of the same shape launches them in plain stream
-    order.  Graph chunks and single launches both give the same bits either way."""
+    order.  Graph chunks and single launches both give the same bits either way, over
+    2000 updates (each update reads only what the update before it wrote, the data the
+    dependent launch's wait makes visible)."""
     from paper_1803_01756_gb300.lattice import Lattice, KERNEL_FUSED_1COL
     w = inputs.workload("channel_4096x512")
     rho0 = inputs.initial_density(w)
@@ -442,7 +444,7 @@ def test_dependent_launch_gives_the_same_bits(monkeypatch):
     def run():
         lat = Lattice(w["nx"], w["ny"], w["params"], kernel=KERNEL_FUSED_1COL)
         lat.write_fields(rho0)
-        lat.step(40)
+        lat.step(2007)
         out, info = lat.read_fields(), lat.info()
         lat.close()
         return out, info
