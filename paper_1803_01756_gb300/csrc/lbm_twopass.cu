@@ -13,8 +13,12 @@
 // recomputes pass A's work on the energy equation's four halo rows as well (its
 // collision stage must deliver u there), and its six stages in one loop body hold
 // enough registers that three CTAs fit an SM; the two passes are lighter and run with
-// more warps per SM.  The price is 24 B per node of extra traffic (rho, u written by A
-// and read by B).
+// more warps per SM (four and five CTAs).  The price is 24 B per node of extra traffic
+// (rho, u written by A and read by B) and a second launch.  Measured on GB300, the path is
+// faster than the fused kernel on small lattices (up to about 2^18 nodes, where the fused
+// kernel's short row chunks spend most row steps filling its pipeline) and slower on large
+// ones (4096 x 512: 75.0 against 65.8 us per update), where the two passes together execute
+// more instructions per node than the fused kernel.
 //
 // Both passes sweep a strip of lattice columns (one column per thread) over a chunk of
 // rows from bottom to top, like the fused kernel, with stages that trail each other in
