@@ -60,9 +60,9 @@ SM_MAX_MHZ = 2070
 # cycle).  They hold for the kernel sources whose hash is FUSED_COUNTERS_SOURCE (the
 # profiles/ summary of the capture records the same hash); when the built sources hash
 # differently the counters are stale and the bench reports them as null.
-FUSED_F32_4096x512_DRAM_BYTES = 103.432448e6 + 40.152576e6
-FUSED_F32_4096x512_WARP_INSTR = 44003952
-FUSED_COUNTERS_SOURCE = "80e58018ed1a4a14"
+FUSED_F32_4096x512_DRAM_BYTES = 103.403264e6 + 39.863040e6
+FUSED_F32_4096x512_WARP_INSTR = 43732808
+FUSED_COUNTERS_SOURCE = "9219133cdaaedea1"
 # the files that determine the fused kernel's machine code
 FUSED_SOURCES = ["paper_1803_01756_gb300/csrc/lbm_common.cuh",
                  "paper_1803_01756_gb300/csrc/lbm_internal.h",
